@@ -1,0 +1,303 @@
+"""Throughput of the coupled IB-LB step (arXiv:2305.18919, Sec. III) on GB300.
+
+Metric: MLUPS including the interface coupling = lattice nodes (wall layers counted) x steps
+/ time of the whole step (face forces, spreading, stream-collide, velocity gather,
+interpolation and update). Default workload: the 256^3 FP32 shear flow with a rigidly coated
+particle (R = 40, icosphere subdivision 6, 40962 vertices, 81920 faces), tau = 0.8, walls
+moving at -/+0.02.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line. With --impl reference the FP64 CPU oracle runs the same workload on the
+host (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2305_18919_gb300 import inputs  # noqa: E402
+
+METRIC = "MLUPS incl. IB coupling"
+
+
+def workload(name: str):
+    if name == "shear256":
+        return inputs.shear_256_fp32()
+    if name == "wetting128":
+        return inputs.wetting_128x128x96()
+    if name == "shear32":
+        return inputs.shear_32_fp64()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, seconds_target=20.0):
+    """The FP64 oracle, as it stands, on a bounded number of full steps of the same workload."""
+    import oracle
+    t0 = time.perf_counter()
+    sim = oracle.Simulation.from_workload(wl)
+    setup = time.perf_counter() - t0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        sim.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target or steps >= 1000:
+            break
+    sim.close()
+    mlups = wl.cells * steps / el / 1e6
+    return {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full IB-LB steps of the {wl.nx}x{wl.ny}x{wl.nz} workload "
+                      f"(FP64 oracle, single thread, {el:.1f} s timed, set-up {setup:.1f} s untimed)"}
+
+
+def run_reference(args, wl, rank):
+    """--impl reference: the oracle on the host, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    t0 = time.perf_counter()
+    sim = oracle.Simulation.from_workload(wl)
+    setup = time.perf_counter() - t0
+    # each oracle step of the full lattice takes seconds; cap the run at about three minutes
+    t1 = time.perf_counter()
+    sim.step(1)
+    one = time.perf_counter() - t1
+    budget = 150.0
+    warm = max(0, min(args.warmup - 1, int(budget * 0.2 / max(one, 1e-9))))
+    sim.step(warm)
+    k = max(1, min(args.steps, int(budget * 0.8 / max(one, 1e-9))))
+    t1 = time.perf_counter()
+    sim.step(k)
+    el = time.perf_counter() - t1
+    sim.close()
+    value = wl.cells * k / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": k, "warmup": warm + 1, "ms_per_step": round(el / k * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(wl),
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{k} full IB-LB steps of the {wl.nx}x{wl.ny}x{wl.nz} workload "
+                                   f"timed of {args.steps} requested (FP64 oracle, single thread; "
+                                   f"set-up {setup:.1f} s untimed)"},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl):
+    v, f = wl.mesh()
+    return {"workload": wl.name, "lattice": [wl.nx, wl.ny, wl.nz], "nodes": wl.cells,
+            "vertices": int(v.shape[0]), "faces": int(f.shape[0]), "tau": wl.tau,
+            "wall_u": [wl.wall_u_bottom[0], wl.wall_u_top[0]],
+            "alpha": list(wl.alpha), "precision": wl.precision,
+            "l2": "no flush: the two population arrays (2 x 1.27 GB) exceed the 129 MB L2"}
+
+
+def run_gpu(args, wl, rank, world):
+    import torch
+    from paper_2305_18919_gb300 import binding
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    lat = binding.Lattice.from_workload(wl, precision=wl.precision)
+    lat.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+
+    # --- device-resident timed region ------------------------------------------------------
+    lat.set_profiling(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        lat.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    k1_ms, k1_launches, launches = lat.profile()
+    lat.set_profiling(False)
+    if dist:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ms_step = ms_total / args.steps
+    value = world * wl.cells * args.steps / (ms_total * 1e-3) / 1e6
+
+    # --- end to end through the C ABI with host buffers -------------------------------------
+    nv = lat.nv
+    q_host = torch.empty((nv, 3), dtype=torch.float64, pin_memory=True).numpy()
+    lat.vertices(out=q_host)
+    e2e_steps = max(1, min(args.steps, 200))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.set_vertices(q_host)   # H2D: this step's vertex positions
+        lat.step(1)
+        lat.vertices(out=q_host)   # D2H: the step's result
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * wl.cells * e2e_steps / e2e_s / 1e6
+
+    bpc = lat.bytes_per_cell()
+    fluid = wl.nx * wl.ny * (wl.nz - 2)
+    k1_avg_ms = k1_ms / max(1, k1_launches)
+    peaks = measured_peaks()
+    if peaks and peaks.get("hbm_gbs"):
+        peak, peak_note = float(peaks["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy)"
+    else:
+        peak, peak_note = 6800.0, "fallback"
+    achieved = bpc * fluid / (k1_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "stream_collide_kernel<float,false>",
+                "algorithmic_bytes_per_launch": bpc * fluid,
+                "k1_ms_avg": round(k1_avg_ms, 5), "peak_source": peak_note,
+                "step_frac": round(bpc * fluid / (ms_step * 1e-3) / 1e9 / peak, 4)}
+    traffic = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
+    if os.path.exists(traffic):
+        try:
+            tr = json.load(open(traffic))
+            if tr.get("workload") == wl.name and tr.get("bytes_per_launch"):
+                roofline["traffic"] = tr["bytes_per_launch"]
+        except Exception:
+            pass
+    clocks = clk.summary()
+    lat.close()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = cpu_baseline(wl, args.cpu_seconds) if (world == 1 and args.cpu_seconds > 0) else None
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config_of(wl), "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "h2d_bytes_per_step": nv * 24,
+                "d2h_bytes_per_step": nv * 24, "steps": e2e_steps,
+                "path": "iblb_set_vertices + iblb_step(1) + iblb_read_vertices, pinned host buffers"},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="shear256")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+    else:
+        run_gpu(args, wl, rank, world)
+
+
+if __name__ == "__main__":
+    main()

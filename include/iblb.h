@@ -1,0 +1,161 @@
+/*
+ * iblb.h -- C ABI of the GB300 (sm_103a) immersed-boundary lattice-Boltzmann library.
+ *
+ * One coupled IB-LB time step of arXiv:2305.18919, Sec. III, in the paper's order:
+ *   1. nodal forces phi = phi^S + phi^V + phi^W on every mesh vertex   (Eqs. 2, 16-19)
+ *   2. spreading F(x) = sum_i phi_i delta_D(x - q_i)                   (Eqs. 13-15)
+ *   3. BGK collision with Guo forcing, then streaming with half-way
+ *      bounce-back walls in z and periodic x, y                         (Eqs. 9-10)
+ *   4. fluid velocity u = (sum_i c_i f_i + F/2) / rho                   (Sec. III, Guo shift)
+ *   5. interpolation qdot_i = sum_x u(x) delta_D(x - q_i)               (Eq. 11)
+ *   6. Euler update q_i += qdot_i                                       (Eq. 12)
+ *
+ * Conventions shared by every call:
+ *  - Lattice units (dx = dt = 1). Layers z = 0 and z = nz-1 are solid wall nodes; the fluid is
+ *    z = 1 .. nz-2 and the bounce-back planes are z = 0.5 and z = nz-1.5. With z_periodic = 1
+ *    there are no walls and every layer is fluid.
+ *  - Host arrays are row-major, x fastest: scalar fields [nz][ny][nx], vector fields
+ *    [nz][ny][nx][3], populations [19][nz][ny][nx], vertices [nv][3], faces [nf][3].
+ *  - Inputs are copied; the caller keeps ownership of every pointer it passes. Outputs are
+ *    written to caller-owned buffers, always in double precision.
+ *  - Every call returns 0 on success or a negative IBLB_E* code; iblb_last_error() then holds a
+ *    one-line message. All device work is ordered on the stream given to iblb_create();
+ *    calls that return data to the host synchronise that stream.
+ *  - The library allocates its own device memory with cudaMalloc and frees it in
+ *    iblb_destroy(). No call falls back to the CPU.
+ *  - D3Q19 ordering inside the library is private; populations are exchanged in the order
+ *    0 rest, 1..6 = +x,-x,+y,-y,+z,-z, 7..18 = (+1,+1,0),(-1,-1,0),(+1,-1,0),(-1,+1,0),
+ *    (+1,0,+1),(-1,0,-1),(+1,0,-1),(-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1).
+ */
+#ifndef IBLB_H
+#define IBLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IBLB_OK 0
+#define IBLB_EINVAL (-1)    /* bad argument: sizes, tau <= 1/2, open or inconsistent mesh */
+#define IBLB_ENOMEM (-2)    /* device allocation failed */
+#define IBLB_ECUDA (-3)     /* a CUDA runtime call failed (message names it) */
+#define IBLB_EUNSTABLE (-4) /* health check failed: NaN, |qdot| >= 0.1, vertex within 0.05 of a
+                               wall plane, or |V/V0 - 1| > 0.05 */
+#define IBLB_ECAPACITY (-5) /* an internal bound was exceeded (active-tile table) */
+
+#define IBLB_FP64 1 /* populations and interface arithmetic in double */
+#define IBLB_FP32 2 /* populations (stored as f_i - w_i rho0) and interface forces in float;
+                       vertex positions and the volume sum stay in double */
+
+typedef struct iblb_ctx iblb_ctx;
+
+/* Lattice description (Sec. III; walls: Sec. III last paragraph; moving walls: Sec. IV). */
+typedef struct {
+  int32_t nx, ny, nz;      /* nx, ny multiples of 4; nz >= 3 with walls, >= 4 periodic */
+  int32_t precision;       /* IBLB_FP64 or IBLB_FP32 */
+  int32_t z_periodic;      /* 0: bounce-back walls at both z ends; 1: periodic z (tests) */
+  int32_t reserved;
+  double tau;              /* BGK relaxation time, > 1/2 (viscosity (tau - 1/2)/3) */
+  double rho0;             /* reference density (initial state and moving-wall term) */
+  double wall_u_bottom[3]; /* wall velocity at z = 0.5 (tangential components only) */
+  double wall_u_top[3];    /* wall velocity at z = nz - 1.5 */
+  double body_force[3];    /* uniform body force density added to the IB force */
+} iblb_lattice_desc;
+
+/* Interface parameters of one mesh: Eq. 2 (alpha), Eq. 18 (kV), Eq. 19 (eps, xi). */
+typedef struct {
+  double alpha[3];         /* (alpha1 pre-stress, alpha2 dilatation, alpha3 shear) */
+  double kV;               /* volume-force coefficient (the paper fixes 1) */
+  double eps;              /* Lennard-Jones strength */
+  double xi;               /* Lennard-Jones length (the paper fixes 0.5) */
+  int32_t wall_force_on;   /* apply Eq. 19 against both wall planes */
+  int32_t volume_force_on; /* apply Eq. 18 */
+} iblb_iface_params;
+
+/* Create a lattice at rest, f = f^eq(rho0, 0) (Eq. 10). `cuda_stream` is a cudaStream_t (NULL:
+   the legacy default stream). On success *out owns all device memory of the context. */
+int iblb_create(const iblb_lattice_desc *desc, void *cuda_stream, iblb_ctx **out);
+
+/* Release every resource of the context (NULL is accepted). Synchronises its stream. */
+void iblb_destroy(iblb_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none). Owned by the context. */
+const char *iblb_last_error(const iblb_ctx *ctx);
+
+/* Add the triangulated interface (Sec. III: refined icosahedron). verts [nv][3], faces [nf][3]
+   oriented counter-clockwise seen from outside. The mesh must be closed and consistently
+   oriented (every edge shared by exactly two faces in opposite directions, nf == 2 nv - 4);
+   this shape becomes the reference shape (per-face metric, V0 = its volume). One mesh per
+   context; *mesh_id receives 0. IBLB_EINVAL otherwise. */
+int iblb_add_mesh(iblb_ctx *ctx, const double *verts, int32_t nv, const int32_t *faces,
+                  int32_t nf, int32_t *mesh_id);
+
+/* Set alpha, kV, eps, xi and the force switches of a mesh (defaults: all alpha 0, kV 1,
+   eps 0, xi 0.5, wall force off, volume force on). */
+int iblb_set_interface(iblb_ctx *ctx, int32_t mesh_id, const iblb_iface_params *params);
+
+/* Replace the current vertex positions (host [nv][3]); the reference shape is unchanged. */
+int iblb_set_vertices(iblb_ctx *ctx, int32_t mesh_id, const double *q);
+
+/* Set every fluid node to f^eq(rho, u) (Eq. 10) of host fields rho [nz][ny][nx] and
+   u [nz][ny][nx][3]; values on wall layers are ignored. */
+int iblb_init_equilibrium(iblb_ctx *ctx, const double *rho, const double *u);
+
+/* Advance nsteps coupled steps (order above). Work is queued on the stream; the call
+   synchronises once at its end to read the health word and returns IBLB_EUNSTABLE or
+   IBLB_ECAPACITY if a check failed during any of the steps. */
+int iblb_step(iblb_ctx *ctx, int32_t nsteps);
+
+/* rho [nz][ny][nx] and u [nz][ny][nx][3] of the current post-streaming state; u carries half
+   of the force of the last spreading step (none before the first step) plus the body force.
+   Wall-layer nodes report rho0 and their wall velocity. */
+int iblb_read_fields(iblb_ctx *ctx, double *rho, double *u);
+
+/* Populations [19][nz][ny][nx] of the current post-streaming state (wall layers: 0). */
+int iblb_read_populations(iblb_ctx *ctx, double *f);
+
+/* Vertex positions [nv][3] (Eq. 12) of the current state. */
+int iblb_read_vertices(iblb_ctx *ctx, int32_t mesh_id, double *q);
+
+/* Same as iblb_read_vertices into a device buffer `q_dev` ([nv][3] doubles, caller-owned),
+   ordered on the context's stream; does not synchronise. */
+int iblb_read_vertices_device(iblb_ctx *ctx, int32_t mesh_id, double *q_dev);
+
+/* Vertex velocities [nv][3] interpolated in the last step (Eq. 11); zero before any step. */
+int iblb_read_vertex_velocities(iblb_ctx *ctx, int32_t mesh_id, double *qdot);
+
+/* Nodal forces phi [nv][3] (Eq. 16) evaluated now at the current vertex positions. */
+int iblb_read_forces(iblb_ctx *ctx, int32_t mesh_id, double *phi);
+
+/* Force density F [nz][ny][nx][3] (Eq. 13) spread now from the forces at the current vertex
+   positions (the interface part only; the body force is not included). */
+int iblb_read_force_field(iblb_ctx *ctx, double *F);
+
+/* Current enclosed volume V (Eq. 18, sum over faces, accumulated in double) and V0. */
+int iblb_read_volume(iblb_ctx *ctx, int32_t mesh_id, double *V, double *V0);
+
+/* Write / read the full state (populations, vertices, reference shape, parameters, step
+   count) to / from a binary file. load_state requires a context created with the same
+   lattice description and a mesh of the same size. */
+int iblb_save_state(iblb_ctx *ctx, const char *path);
+int iblb_load_state(iblb_ctx *ctx, const char *path);
+
+/* Number of steps taken so far. */
+int64_t iblb_steps_done(const iblb_ctx *ctx);
+
+/* Profiling of the dominant kernel. When on, iblb_step() brackets every stream-collide launch
+   with CUDA events on the context's stream. iblb_profile() synchronises and returns the summed
+   stream-collide time in milliseconds, the number of stream-collide launches and the number of
+   kernel launches made by iblb_step() since profiling was switched on. */
+int iblb_set_profiling(iblb_ctx *ctx, int32_t on);
+int iblb_profile(iblb_ctx *ctx, double *k1_ms, int64_t *k1_launches, int64_t *kernel_launches);
+
+/* Bytes moved per fluid cell by one stream-collide launch (19 loads + 19 stores of the
+   population type): 152 for IBLB_FP32, 304 for IBLB_FP64. */
+int64_t iblb_bytes_per_cell(const iblb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBLB_H */

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of the C ABI in include/iblb.h (argument marshalling only).
+
+Every call goes to the CUDA library ``_build/libiblb.so``; there is no CPU path. If the
+library cannot be built or loaded the import raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+IBLB_OK = 0
+IBLB_EINVAL = -1
+IBLB_ENOMEM = -2
+IBLB_ECUDA = -3
+IBLB_EUNSTABLE = -4
+IBLB_ECAPACITY = -5
+IBLB_FP64 = 1
+IBLB_FP32 = 2
+
+_PRECISION = {"fp64": IBLB_FP64, "fp32": IBLB_FP32}
+
+
+class iblb_lattice_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("z_periodic", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("wall_u_bottom", ctypes.c_double * 3), ("wall_u_top", ctypes.c_double * 3),
+                ("body_force", ctypes.c_double * 3)]
+
+
+class iblb_iface_params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double * 3), ("kV", ctypes.c_double), ("eps", ctypes.c_double),
+                ("xi", ctypes.c_double), ("wall_force_on", ctypes.c_int32),
+                ("volume_force_on", ctypes.c_int32)]
+
+
+class IBLBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"iblb error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+# name -> (restype, argtypes); the exported surface of include/iblb.h
+SIGNATURES = {
+    "iblb_create": (_i32, [ctypes.POINTER(iblb_lattice_desc), _vp, ctypes.POINTER(_vp)]),
+    "iblb_destroy": (None, [_vp]),
+    "iblb_last_error": (ctypes.c_char_p, [_vp]),
+    "iblb_add_mesh": (_i32, [_vp, _dp, _i32, _ip, _i32, _ip]),
+    "iblb_set_interface": (_i32, [_vp, _i32, ctypes.POINTER(iblb_iface_params)]),
+    "iblb_set_vertices": (_i32, [_vp, _i32, _dp]),
+    "iblb_init_equilibrium": (_i32, [_vp, _dp, _dp]),
+    "iblb_step": (_i32, [_vp, _i32]),
+    "iblb_read_fields": (_i32, [_vp, _dp, _dp]),
+    "iblb_read_populations": (_i32, [_vp, _dp]),
+    "iblb_read_vertices": (_i32, [_vp, _i32, _dp]),
+    "iblb_read_vertices_device": (_i32, [_vp, _i32, _vp]),
+    "iblb_read_vertex_velocities": (_i32, [_vp, _i32, _dp]),
+    "iblb_read_forces": (_i32, [_vp, _i32, _dp]),
+    "iblb_read_force_field": (_i32, [_vp, _dp]),
+    "iblb_read_volume": (_i32, [_vp, _i32, _dp, _dp]),
+    "iblb_save_state": (_i32, [_vp, ctypes.c_char_p]),
+    "iblb_load_state": (_i32, [_vp, ctypes.c_char_p]),
+    "iblb_steps_done": (_i64, [_vp]),
+    "iblb_set_profiling": (_i32, [_vp, _i32]),
+    "iblb_profile": (_i32, [_vp, _dp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "iblb_bytes_per_cell": (_i64, [_vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if needed) the CUDA library; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _current_stream():
+    """torch's current CUDA stream handle, or None (legacy default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return None
+
+
+class Lattice:
+    """One IB-LB context (lattice + optional interface mesh) on the current CUDA device."""
+
+    def __init__(self, nx, ny, nz, tau, rho0=1.0, wall_u_bottom=(0, 0, 0), wall_u_top=(0, 0, 0),
+                 body_force=(0, 0, 0), precision="fp32", z_periodic=False, stream=None):
+        self._L = lib()
+        d = iblb_lattice_desc()
+        d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+        d.precision = _PRECISION[precision] if isinstance(precision, str) else int(precision)
+        d.z_periodic = int(bool(z_periodic))
+        d.tau, d.rho0 = float(tau), float(rho0)
+        d.wall_u_bottom[:] = [float(v) for v in wall_u_bottom]
+        d.wall_u_top[:] = [float(v) for v in wall_u_top]
+        d.body_force[:] = [float(v) for v in body_force]
+        self.shape = (int(nx), int(ny), int(nz))
+        self.precision = precision
+        self.nv = 0
+        self.nf = 0
+        self.h = ctypes.c_void_p()
+        s = stream if stream is not None else _current_stream()
+        rc = self._L.iblb_create(ctypes.byref(d), s, ctypes.byref(self.h))
+        if rc != IBLB_OK:
+            raise IBLBError(rc, "iblb_create failed (invalid description or CUDA unavailable)")
+
+    @classmethod
+    def from_workload(cls, wl, precision=None, z_periodic=False, stream=None):
+        lat = cls(wl.nx, wl.ny, wl.nz, wl.tau, 1.0, wl.wall_u_bottom, wl.wall_u_top,
+                  wl.body_force, precision or wl.precision, z_periodic, stream)
+        v, f = wl.mesh()
+        lat.add_mesh(v, f)
+        lat.set_interface(wl.alpha, wl.kV, wl.eps, wl.xi, wl.wall_force_on, wl.volume_force_on)
+        return lat
+
+    def _check(self, rc):
+        if rc != IBLB_OK:
+            msg = self._L.iblb_last_error(self.h)
+            raise IBLBError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if self.h:
+            self._L.iblb_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- set-up --------------------------------------------------------------------
+    def add_mesh(self, verts, faces) -> int:
+        v = _f64(verts)
+        f = np.ascontiguousarray(faces, dtype=np.int32)
+        mid = _i32()
+        self._check(self._L.iblb_add_mesh(self.h, _dptr(v), v.shape[0], f.ctypes.data_as(_ip),
+                                          f.shape[0], ctypes.byref(mid)))
+        self.nv, self.nf = v.shape[0], f.shape[0]
+        return mid.value
+
+    def set_interface(self, alpha, kV=1.0, eps=0.0, xi=0.5, wall_force_on=0, volume_force_on=1,
+                      mesh_id=0):
+        p = iblb_iface_params()
+        p.alpha[:] = [float(a) for a in alpha]
+        p.kV, p.eps, p.xi = float(kV), float(eps), float(xi)
+        p.wall_force_on, p.volume_force_on = int(wall_force_on), int(volume_force_on)
+        self._check(self._L.iblb_set_interface(self.h, mesh_id, ctypes.byref(p)))
+
+    def set_vertices(self, q, mesh_id=0):
+        q = _f64(q, (self.nv, 3))
+        self._check(self._L.iblb_set_vertices(self.h, mesh_id, _dptr(q)))
+
+    def init_equilibrium(self, rho, u):
+        nx, ny, nz = self.shape
+        self._check(self._L.iblb_init_equilibrium(self.h, _dptr(_f64(rho, (nz, ny, nx))),
+                                                  _dptr(_f64(u, (nz, ny, nx, 3)))))
+
+    # --- stepping ------------------------------------------------------------------
+    def step(self, n=1):
+        self._check(self._L.iblb_step(self.h, int(n)))
+
+    @property
+    def steps_done(self) -> int:
+        return int(self._L.iblb_steps_done(self.h))
+
+    # --- read-back -----------------------------------------------------------------
+    def fields(self):
+        nx, ny, nz = self.shape
+        rho = np.empty((nz, ny, nx))
+        u = np.empty((nz, ny, nx, 3))
+        self._check(self._L.iblb_read_fields(self.h, _dptr(rho), _dptr(u)))
+        return rho, u
+
+    def populations(self):
+        nx, ny, nz = self.shape
+        f = np.empty((19, nz, ny, nx))
+        self._check(self._L.iblb_read_populations(self.h, _dptr(f)))
+        return f
+
+    def vertices(self, out=None, mesh_id=0):
+        q = np.empty((self.nv, 3)) if out is None else out
+        self._check(self._L.iblb_read_vertices(self.h, mesh_id, _dptr(q)))
+        return q
+
+    def vertices_device(self, out_ptr: int, mesh_id=0):
+        self._check(self._L.iblb_read_vertices_device(self.h, mesh_id, ctypes.c_void_p(out_ptr)))
+
+    def vertex_velocities(self, mesh_id=0):
+        q = np.empty((self.nv, 3))
+        self._check(self._L.iblb_read_vertex_velocities(self.h, mesh_id, _dptr(q)))
+        return q
+
+    def forces(self, mesh_id=0):
+        phi = np.empty((self.nv, 3))
+        self._check(self._L.iblb_read_forces(self.h, mesh_id, _dptr(phi)))
+        return phi
+
+    def force_field(self):
+        nx, ny, nz = self.shape
+        F = np.empty((nz, ny, nx, 3))
+        self._check(self._L.iblb_read_force_field(self.h, _dptr(F)))
+        return F
+
+    def volume(self, mesh_id=0):
+        V = ctypes.c_double()
+        V0 = ctypes.c_double()
+        self._check(self._L.iblb_read_volume(self.h, mesh_id, ctypes.byref(V), ctypes.byref(V0)))
+        return V.value, V0.value
+
+    def save_state(self, path):
+        self._check(self._L.iblb_save_state(self.h, os.fsencode(path)))
+
+    def load_state(self, path):
+        self._check(self._L.iblb_load_state(self.h, os.fsencode(path)))
+
+    # --- profiling -----------------------------------------------------------------
+    def set_profiling(self, on=True):
+        self._check(self._L.iblb_set_profiling(self.h, int(bool(on))))
+
+    def profile(self):
+        ms = ctypes.c_double()
+        k1 = _i64()
+        kl = _i64()
+        self._check(self._L.iblb_profile(self.h, ctypes.byref(ms), ctypes.byref(k1), ctypes.byref(kl)))
+        return ms.value, k1.value, kl.value
+
+    def bytes_per_cell(self) -> int:
+        return int(self._L.iblb_bytes_per_cell(self.h))

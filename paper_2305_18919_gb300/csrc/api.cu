@@ -1,0 +1,631 @@
+// C ABI of the IB-LB library (declared in include/iblb.h): context management, mesh set-up
+// (reference metric, vertex->face lists), the step driver in the order of Sec. III, and the
+// read-back, checkpoint and profiling calls.
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <unordered_map>
+#include <vector>
+
+#include "iblb_internal.cuh"
+
+using iblb::Ctx;
+
+struct iblb_ctx {
+  Ctx c;
+};
+
+namespace {
+
+int fail(Ctx &c, int code, const std::string &msg) {
+  c.err = msg;
+  return code;
+}
+
+#define CUDA_TRY(c, expr)                                                               \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail((c), e_ == cudaErrorMemoryAllocation ? IBLB_ENOMEM : IBLB_ECUDA,       \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+cudaError_t dalloc_bytes(void **p, size_t bytes) {
+  *p = nullptr;
+  return cudaMalloc(p, bytes ? bytes : 1);
+}
+
+void dfree(void *p) {
+  if (p) cudaFree(p);
+}
+
+int staging(Ctx &c, size_t n_doubles) {
+  if (c.dscratch_len >= n_doubles) return 0;
+  dfree(c.dscratch);
+  c.dscratch = nullptr;
+  c.dscratch_len = 0;
+  CUDA_TRY(c, dalloc(&c.dscratch, n_doubles));
+  c.dscratch_len = n_doubles;
+  return 0;
+}
+
+int check_mesh_id(Ctx &c, int mesh_id) {
+  if (c.nv == 0) return fail(c, IBLB_EINVAL, "no mesh has been added");
+  if (mesh_id != 0) return fail(c, IBLB_EINVAL, "unknown mesh id");
+  return 0;
+}
+
+// Clear a tile map and mark it for the current vertex positions.
+int remark(Ctx &c, int which) {
+  CUDA_TRY(c, cudaMemsetAsync(c.tile_slot[which], 0xff, c.ntiles * sizeof(int), c.stream));
+  CUDA_TRY(c, cudaMemsetAsync(c.counters + which, 0, sizeof(int), c.stream));
+  const int saved = c.map;
+  c.map = which;
+  cudaError_t e = iblb::launch_mark(c);
+  c.map = saved;
+  CUDA_TRY(c, e);
+  return 0;
+}
+
+int read_health(Ctx &c, int *h) {
+  CUDA_TRY(c, cudaMemcpyAsync(h, c.counters + 3, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  return 0;
+}
+
+int health_error(Ctx &c, int h) {
+  if (h & iblb::H_CAPACITY) return fail(c, IBLB_ECAPACITY, "active-tile table capacity exceeded");
+  std::string m = "health check failed:";
+  if (h & iblb::H_NAN) m += " NaN in vertex velocity;";
+  if (h & iblb::H_FAST) m += " |qdot| >= 0.1;";
+  if (h & iblb::H_WALL) m += " vertex within 0.05 of a wall plane;";
+  if (h & iblb::H_VOLUME) m += " |V/V0 - 1| > 0.05;";
+  return fail(c, IBLB_EUNSTABLE, m);
+}
+
+cudaEvent_t pooled_event(Ctx &c) {
+  if (c.ev_used == c.ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c.ev_pool.push_back(e);
+  }
+  return c.ev_pool[c.ev_used++];
+}
+
+}  // namespace
+
+extern "C" {
+
+int iblb_create(const iblb_lattice_desc *d, void *cuda_stream, iblb_ctx **out) {
+  if (!out) return IBLB_EINVAL;
+  *out = nullptr;
+  if (!d) return IBLB_EINVAL;
+  const int periodic = d->z_periodic ? 1 : 0;
+  if (d->nx < 4 || d->ny < 4 || d->nx % 4 || d->ny % 4 || d->nz < (periodic ? 4 : 3) ||
+      (periodic && d->nz % 4) || !(d->tau > 0.5) || !(d->rho0 > 0) ||
+      (d->precision != IBLB_FP32 && d->precision != IBLB_FP64))
+    return IBLB_EINVAL;
+  if (!periodic && (d->wall_u_bottom[2] != 0.0 || d->wall_u_top[2] != 0.0)) return IBLB_EINVAL;
+  iblb_ctx *h = new iblb_ctx();
+  Ctx &c = h->c;
+  c.nx = d->nx; c.ny = d->ny; c.nz = d->nz;
+  c.precision = d->precision;
+  c.has_walls = !periodic;
+  c.tau = d->tau;
+  c.rho0 = d->rho0;
+  for (int k = 0; k < 3; k++) {
+    c.ub[k] = d->wall_u_bottom[k];
+    c.ut[k] = d->wall_u_top[k];
+    c.g[k] = d->body_force[k];
+  }
+  c.stream = (cudaStream_t)cuda_stream;
+  c.ncell = (size_t)c.nx * c.ny * c.nz;
+  c.real_size = c.precision == IBLB_FP64 ? 8 : 4;
+  c.ntx = c.nx / 4;
+  c.nty = c.ny / 4;
+  c.ntz = (c.nz + 3) / 4;
+  c.ntiles = (size_t)c.ntx * c.nty * c.ntz;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev);
+  for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc_bytes(&c.f[b], (size_t)iblb::Q * c.ncell * c.real_size);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.f[0], 0, (size_t)iblb::Q * c.ncell * c.real_size, c.stream);
+  // the interface chain gets the highest stream priority so its small kernels are scheduled
+  // between the blocks of the concurrent full-lattice pass instead of after it
+  int prio_lo = 0, prio_hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c.ib, cudaStreamNonBlocking, prio_hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_force, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_coll, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_sync, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = dalloc(&c.counters, 8);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.counters, 0, 8 * sizeof(int), c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    iblb_destroy(h);
+    return e == cudaErrorMemoryAllocation ? IBLB_ENOMEM : IBLB_ECUDA;
+  }
+  *out = h;
+  return IBLB_OK;
+}
+
+void iblb_destroy(iblb_ctx *h) {
+  if (!h) return;
+  Ctx &c = h->c;
+  cudaStreamSynchronize(c.stream);
+  if (c.ib) cudaStreamSynchronize(c.ib);
+  for (int b = 0; b < 2; b++) {
+    dfree(c.f[b]);
+    dfree(c.tile_slot[b]);
+    dfree(c.slot_tile[b]);
+    dfree(c.Fslot[b]);
+  }
+  dfree(c.counters); dfree(c.slot_count); dfree(c.bucket); dfree(c.overflow); dfree(c.Uslot);
+  dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.vf_start); dfree(c.vf_list);
+  dfree(c.fcontrib); dfree(c.fnorm); dfree(c.vol_partial); dfree(c.phi); dfree(c.stencil);
+  dfree(c.dscratch);
+  for (cudaEvent_t ev : c.ev_pool) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : c.ev_near) cudaEventDestroy(ev);
+  if (c.ev_force) cudaEventDestroy(c.ev_force);
+  if (c.ev_coll) cudaEventDestroy(c.ev_coll);
+  if (c.ev_sync) cudaEventDestroy(c.ev_sync);
+  if (c.ib) cudaStreamDestroy(c.ib);
+  delete h;
+}
+
+const char *iblb_last_error(const iblb_ctx *h) { return h ? h->c.err.c_str() : "null context"; }
+
+int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *faces, int32_t nf,
+                  int32_t *mesh_id) {
+  if (!h) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (c.nv) return fail(c, IBLB_EINVAL, "one mesh per context");
+  if (!verts || !faces || nv < 4 || nf != 2 * nv - 4)
+    return fail(c, IBLB_EINVAL, "mesh must be closed: nf == 2 nv - 4, nv >= 4");
+  // closedness and orientation: each directed edge once, its reverse once
+  std::unordered_map<uint64_t, int> edges;
+  edges.reserve((size_t)3 * nf * 2);
+  for (int j = 0; j < nf; j++) {
+    for (int k = 0; k < 3; k++) {
+      const int a = faces[3 * j + k], b = faces[3 * j + (k + 1) % 3];
+      if (a < 0 || a >= nv || b < 0 || b >= nv || a == b)
+        return fail(c, IBLB_EINVAL, "face index out of range or degenerate face");
+      const uint64_t key = ((uint64_t)(uint32_t)a << 32) | (uint32_t)b;
+      if (edges.count(key)) return fail(c, IBLB_EINVAL, "directed edge used twice: inconsistent orientation");
+      edges[key] = j;
+    }
+  }
+  for (const auto &kv : edges) {
+    const uint64_t rev = (kv.first << 32) | (kv.first >> 32);
+    if (!edges.count(rev)) return fail(c, IBLB_EINVAL, "open mesh: an edge has one face");
+  }
+  for (int i = 0; i < 3 * nv; i++)
+    if (!std::isfinite(verts[i])) return fail(c, IBLB_EINVAL, "non-finite vertex coordinate");
+  // reference shape: centre, per-face inverse metric and area, volume
+  double centre[3] = {0, 0, 0};
+  for (int i = 0; i < nv; i++)
+    for (int k = 0; k < 3; k++) centre[k] += verts[3 * i + k] / nv;
+  std::vector<double> fref((size_t)4 * nf);
+  double V0 = 0.0;
+  for (int j = 0; j < nf; j++) {
+    const double *X0 = verts + 3 * faces[3 * j], *X1 = verts + 3 * faces[3 * j + 1],
+                 *X2 = verts + 3 * faces[3 * j + 2];
+    double a[3], b[3], r0[3], r1[3], r2[3];
+    for (int k = 0; k < 3; k++) {
+      a[k] = X1[k] - X0[k];
+      b[k] = X2[k] - X0[k];
+      r0[k] = X0[k] - centre[k];
+      r1[k] = X1[k] - centre[k];
+      r2[k] = X2[k] - centre[k];
+    }
+    const double g11 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    const double g12 = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    const double g22 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const double det = g11 * g22 - g12 * g12;
+    if (!(det > 0)) return fail(c, IBLB_EINVAL, "degenerate reference face");
+    fref[4 * j] = g22 / det;
+    fref[4 * j + 1] = -g12 / det;
+    fref[4 * j + 2] = g11 / det;
+    fref[4 * j + 3] = 0.5 * std::sqrt(det);
+    V0 += (r0[0] * (r1[1] * r2[2] - r1[2] * r2[1]) + r0[1] * (r1[2] * r2[0] - r1[0] * r2[2]) +
+           r0[2] * (r1[0] * r2[1] - r1[1] * r2[0])) / 6.0;
+  }
+  if (!(V0 > 0)) return fail(c, IBLB_EINVAL, "mesh is not oriented outward (volume <= 0)");
+  // vertex -> (face, corner) lists in face order
+  std::vector<int> vf_start(nv + 1, 0), vf_list((size_t)3 * nf);
+  for (int j = 0; j < 3 * nf; j++) vf_start[faces[j] + 1]++;
+  for (int i = 0; i < nv; i++) vf_start[i + 1] += vf_start[i];
+  {
+    std::vector<int> fill(vf_start.begin(), vf_start.end() - 1);
+    for (int j = 0; j < nf; j++)
+      for (int k = 0; k < 3; k++) vf_list[fill[faces[3 * j + k]]++] = 3 * j + k;
+  }
+  c.nv = nv;
+  c.nf = nf;
+  c.V0 = V0;
+  for (int k = 0; k < 3; k++) c.centre[k] = centre[k];
+  c.vol_blocks = (nf + 255) / 256;
+  const size_t rs = c.real_size;
+  long ms = 8L * nv;
+  if ((size_t)ms > c.ntiles) ms = (long)c.ntiles;
+  c.max_slots = (int)ms;
+  // iface defaults
+  c.iface.alpha[0] = c.iface.alpha[1] = c.iface.alpha[2] = 0.0;
+  c.iface.kV = 1.0;
+  c.iface.eps = 0.0;
+  c.iface.xi = 0.5;
+  c.iface.wall_force_on = 0;
+  c.iface.volume_force_on = 1;
+  CUDA_TRY(c, dalloc(&c.q, (size_t)3 * nv));
+  CUDA_TRY(c, dalloc(&c.qdot, (size_t)3 * nv));
+  CUDA_TRY(c, dalloc(&c.faces, (size_t)3 * nf));
+  CUDA_TRY(c, dalloc(&c.fref, (size_t)4 * nf));
+  CUDA_TRY(c, dalloc(&c.vf_start, (size_t)nv + 1));
+  CUDA_TRY(c, dalloc(&c.vf_list, (size_t)3 * nf));
+  CUDA_TRY(c, dalloc_bytes(&c.fcontrib, (size_t)9 * nf * rs));
+  CUDA_TRY(c, dalloc_bytes(&c.fnorm, (size_t)3 * nf * rs));
+  CUDA_TRY(c, dalloc(&c.vol_partial, (size_t)c.vol_blocks));
+  CUDA_TRY(c, dalloc_bytes(&c.phi, (size_t)3 * nv * rs));
+  CUDA_TRY(c, dalloc_bytes(&c.stencil, (size_t)nv * iblb::stencil_record_bytes(c)));
+  for (int b = 0; b < 2; b++) {
+    CUDA_TRY(c, dalloc(&c.tile_slot[b], c.ntiles));
+    CUDA_TRY(c, dalloc(&c.slot_tile[b], (size_t)c.max_slots));
+    CUDA_TRY(c, dalloc_bytes(&c.Fslot[b], (size_t)c.max_slots * 3 * iblb::TILE_CELLS * rs));
+    CUDA_TRY(c, cudaMemsetAsync(c.tile_slot[b], 0xff, c.ntiles * sizeof(int), c.stream));
+  }
+  CUDA_TRY(c, dalloc(&c.slot_count, (size_t)c.max_slots));
+  CUDA_TRY(c, dalloc(&c.bucket, (size_t)c.max_slots * iblb::BUCKET_CAP));
+  CUDA_TRY(c, dalloc(&c.overflow, (size_t)nv));
+  CUDA_TRY(c, dalloc_bytes(&c.Uslot, (size_t)c.max_slots * 3 * iblb::TILE_CELLS * rs));
+  CUDA_TRY(c, cudaMemsetAsync(c.counters, 0, 8 * sizeof(int), c.stream));
+  CUDA_TRY(c, cudaMemsetAsync(c.qdot, 0, (size_t)3 * nv * sizeof(double), c.stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c.q, verts, (size_t)3 * nv * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c.faces, faces, (size_t)3 * nf * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c.vf_start, vf_start.data(), (size_t)(nv + 1) * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c.vf_list, vf_list.data(), (size_t)3 * nf * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c.fref, fref.data(), fref.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  c.map = 0;
+  c.have_force = 0;
+  int rc = remark(c, 0);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  if (mesh_id) *mesh_id = 0;
+  return IBLB_OK;
+}
+
+int iblb_set_interface(iblb_ctx *h, int32_t mesh_id, const iblb_iface_params *p) {
+  if (!h || !p) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = check_mesh_id(c, mesh_id)) return rc;
+  for (int k = 0; k < 3; k++)
+    if (!std::isfinite(p->alpha[k])) return fail(c, IBLB_EINVAL, "non-finite alpha");
+  if (!std::isfinite(p->kV) || !std::isfinite(p->eps) || !(p->xi > 0))
+    return fail(c, IBLB_EINVAL, "invalid kV, eps or xi");
+  c.iface = *p;
+  return IBLB_OK;
+}
+
+int iblb_set_vertices(iblb_ctx *h, int32_t mesh_id, const double *q) {
+  if (!h || !q) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = check_mesh_id(c, mesh_id)) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(c.q, q, (size_t)3 * c.nv * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  // the map of the last spreading step (map ^ 1) stays: read_fields still uses its force
+  return remark(c, c.map);
+}
+
+int iblb_init_equilibrium(iblb_ctx *h, const double *rho, const double *u) {
+  if (!h || !rho || !u) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = staging(c, 4 * c.ncell)) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(c.dscratch, rho, c.ncell * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c.dscratch + c.ncell, u, 3 * c.ncell * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  CUDA_TRY(c, iblb::launch_init_equilibrium(c, c.dscratch, c.dscratch + c.ncell));
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  c.fresh = 1;
+  c.have_force = 0;
+  return IBLB_OK;
+}
+
+// One step in the order of Sec. III on two streams. The interface chain (forces, spreading;
+// after the collision: velocity gather, interpolation, update, marking) runs on the library
+// stream `ib`. The stream-collide of every node with the body force only runs on the
+// caller's stream without waiting for it, so it overlaps the interface chain of the same
+// step and the tail of the previous one; then the nodes of the active tiles are collided
+// again once the spread force is ready.
+int iblb_step(iblb_ctx *h, int32_t nsteps) {
+  if (!h) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (nsteps < 0) return fail(c, IBLB_EINVAL, "nsteps < 0");
+  if (nsteps == 0) return IBLB_OK;
+  CUDA_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
+  // the library stream starts after everything queued so far on the caller's stream
+  CUDA_TRY(c, cudaEventRecord(c.ev_sync, c.stream));
+  CUDA_TRY(c, cudaStreamWaitEvent(c.ib, c.ev_sync, 0));
+  for (int s = 0; s < nsteps; s++) {
+    if (c.nv) {
+      CUDA_TRY(c, iblb::launch_face_forces(c, 1, c.ib));
+      CUDA_TRY(c, iblb::launch_vertex_forces(c, 2, c.ib));
+      CUDA_TRY(c, iblb::launch_spread(c, c.ib));
+      CUDA_TRY(c, cudaEventRecord(c.ev_force, c.ib));
+      c.kernel_launches += 3;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c.profiling) {
+      e0 = pooled_event(c);
+      e1 = pooled_event(c);
+      if (!e0 || !e1) return fail(c, IBLB_ECUDA, "cudaEventCreate failed");
+      CUDA_TRY(c, cudaEventRecord(e0, c.stream));
+    }
+    CUDA_TRY(c, iblb::launch_stream_collide(c, c.fresh, c.stream));
+    if (c.profiling) CUDA_TRY(c, cudaEventRecord(e1, c.stream));
+    c.k1_launches += 1;
+    c.kernel_launches += 1;
+    if (c.nv) {
+      CUDA_TRY(c, cudaStreamWaitEvent(c.stream, c.ev_force, 0));
+      CUDA_TRY(c, iblb::launch_stream_collide_tiles(c, c.fresh, c.stream));
+      CUDA_TRY(c, cudaEventRecord(c.ev_coll, c.stream));
+      c.kernel_launches += 1;
+    }
+    c.cur ^= 1;
+    c.fresh = 0;
+    if (c.nv) {
+      CUDA_TRY(c, cudaStreamWaitEvent(c.ib, c.ev_coll, 0));
+      CUDA_TRY(c, iblb::launch_shell_velocity(c, c.ib));
+      CUDA_TRY(c, iblb::launch_interpolate_advect(c, c.ib));
+      c.kernel_launches += 2;
+      c.map ^= 1;
+      c.have_force = 1;
+    }
+    c.steps_done++;
+  }
+  // the caller's stream continues after the interface chain of the last step
+  CUDA_TRY(c, cudaEventRecord(c.ev_sync, c.ib));
+  CUDA_TRY(c, cudaStreamWaitEvent(c.stream, c.ev_sync, 0));
+  int hw = 0;
+  if (int rc = read_health(c, &hw)) return rc;
+  if (hw) return health_error(c, hw);
+  return IBLB_OK;
+}
+
+int iblb_read_fields(iblb_ctx *h, double *rho, double *u) {
+  if (!h || !rho || !u) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = staging(c, 4 * c.ncell)) return rc;
+  CUDA_TRY(c, iblb::launch_fields(c, c.dscratch, c.dscratch + c.ncell));
+  CUDA_TRY(c, cudaMemcpyAsync(rho, c.dscratch, c.ncell * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(c, cudaMemcpyAsync(u, c.dscratch + c.ncell, 3 * c.ncell * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  return IBLB_OK;
+}
+
+int iblb_read_populations(iblb_ctx *h, double *f) {
+  if (!h || !f) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = staging(c, (size_t)iblb::Q * c.ncell)) return rc;
+  CUDA_TRY(c, iblb::launch_populations(c, c.dscratch));
+  CUDA_TRY(c, cudaMemcpyAsync(f, c.dscratch, (size_t)iblb::Q * c.ncell * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  return IBLB_OK;
+}
+
+int iblb_read_vertices(iblb_ctx *h, int32_t mesh_id, double *q) {
+  if (!h || !q) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = check_mesh_id(c, mesh_id)) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(q, c.q, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  return IBLB_OK;
+}
+
+int iblb_read_vertices_device(iblb_ctx *h, int32_t mesh_id, double *q_dev) {
+  if (!h || !q_dev) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = check_mesh_id(c, mesh_id)) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(q_dev, c.q, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  return IBLB_OK;
+}
+
+int iblb_read_vertex_velocities(iblb_ctx *h, int32_t mesh_id, double *qdot) {
+  if (!h || !qdot) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = check_mesh_id(c, mesh_id)) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(qdot, c.qdot, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  return IBLB_OK;
+}
+
+int iblb_read_forces(iblb_ctx *h, int32_t mesh_id, double *phi) {
+  if (!h || !phi) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = check_mesh_id(c, mesh_id)) return rc;
+  if (int rc = staging(c, (size_t)3 * c.nv)) return rc;
+  CUDA_TRY(c, iblb::launch_face_forces(c, 0, c.stream));
+  CUDA_TRY(c, iblb::launch_vertex_forces(c, 0, c.stream));
+  CUDA_TRY(c, iblb::launch_phi_to_double(c, c.dscratch));
+  CUDA_TRY(c, cudaMemcpyAsync(phi, c.dscratch, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  return IBLB_OK;
+}
+
+int iblb_read_force_field(iblb_ctx *h, double *F) {
+  if (!h || !F) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = staging(c, 3 * c.ncell)) return rc;
+  CUDA_TRY(c, cudaMemsetAsync(c.dscratch, 0, 3 * c.ncell * sizeof(double), c.stream));
+  if (c.nv) {
+    CUDA_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
+    CUDA_TRY(c, iblb::launch_face_forces(c, 0, c.stream));
+    CUDA_TRY(c, iblb::launch_vertex_forces(c, 1, c.stream));
+    CUDA_TRY(c, iblb::launch_spread(c, c.stream));
+    CUDA_TRY(c, iblb::launch_expand_force(c, c.dscratch));
+    CUDA_TRY(c, iblb::launch_clear_counts(c));
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(F, c.dscratch, 3 * c.ncell * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  if (c.nv) {
+    int hw = 0;
+    if (int rc = read_health(c, &hw)) return rc;
+    if (hw & iblb::H_CAPACITY) return health_error(c, iblb::H_CAPACITY);
+  }
+  return IBLB_OK;
+}
+
+int iblb_read_volume(iblb_ctx *h, int32_t mesh_id, double *V, double *V0) {
+  if (!h || !V || !V0) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (int rc = check_mesh_id(c, mesh_id)) return rc;
+  if (int rc = staging(c, 1)) return rc;
+  CUDA_TRY(c, iblb::launch_face_forces(c, 0, c.stream));
+  CUDA_TRY(c, iblb::launch_volume(c, c.dscratch));
+  CUDA_TRY(c, cudaMemcpyAsync(V, c.dscratch, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  *V0 = c.V0;
+  return IBLB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Checkpoint: header + populations (as stored) + mesh state.
+// ---------------------------------------------------------------------------------------
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t nx, ny, nz, precision, has_walls, nv, nf, fresh;
+  int64_t steps_done;
+  double tau, rho0, ub[3], ut[3], g[3], V0, centre[3];
+  iblb_iface_params iface;
+};
+}  // namespace
+
+int iblb_save_state(iblb_ctx *h, const char *path) {
+  if (!h || !path) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  StateHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, "IBLBST01", 8);
+  hd.nx = c.nx; hd.ny = c.ny; hd.nz = c.nz; hd.precision = c.precision; hd.has_walls = c.has_walls;
+  hd.nv = c.nv; hd.nf = c.nf; hd.fresh = c.fresh; hd.steps_done = c.steps_done;
+  hd.tau = c.tau; hd.rho0 = c.rho0; hd.V0 = c.V0;
+  for (int k = 0; k < 3; k++) {
+    hd.ub[k] = c.ub[k]; hd.ut[k] = c.ut[k]; hd.g[k] = c.g[k]; hd.centre[k] = c.centre[k];
+  }
+  hd.iface = c.iface;
+  const size_t fbytes = (size_t)iblb::Q * c.ncell * c.real_size;
+  std::vector<char> fbuf(fbytes);
+  std::vector<double> qbuf((size_t)3 * c.nv), qdbuf((size_t)3 * c.nv);
+  std::vector<char> refbuf((size_t)4 * c.nf * sizeof(double));
+  std::vector<int> fcs((size_t)3 * c.nf);
+  CUDA_TRY(c, cudaMemcpyAsync(fbuf.data(), c.f[c.cur], fbytes, cudaMemcpyDeviceToHost, c.stream));
+  if (c.nv) {
+    CUDA_TRY(c, cudaMemcpyAsync(qbuf.data(), c.q, qbuf.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(c, cudaMemcpyAsync(qdbuf.data(), c.qdot, qdbuf.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(c, cudaMemcpyAsync(refbuf.data(), c.fref, refbuf.size(), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(c, cudaMemcpyAsync(fcs.data(), c.faces, fcs.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  FILE *fp = fopen(path, "wb");
+  if (!fp) return fail(c, IBLB_EINVAL, std::string("cannot open for writing: ") + path);
+  bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1 && fwrite(fbuf.data(), 1, fbytes, fp) == fbytes;
+  if (c.nv) {
+    ok = ok && fwrite(qbuf.data(), sizeof(double), qbuf.size(), fp) == qbuf.size();
+    ok = ok && fwrite(qdbuf.data(), sizeof(double), qdbuf.size(), fp) == qdbuf.size();
+    ok = ok && fwrite(refbuf.data(), 1, refbuf.size(), fp) == refbuf.size();
+    ok = ok && fwrite(fcs.data(), sizeof(int), fcs.size(), fp) == fcs.size();
+  }
+  ok = (fclose(fp) == 0) && ok;
+  if (!ok) return fail(c, IBLB_EINVAL, std::string("write failed: ") + path);
+  return IBLB_OK;
+}
+
+int iblb_load_state(iblb_ctx *h, const char *path) {
+  if (!h || !path) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  FILE *fp = fopen(path, "rb");
+  if (!fp) return fail(c, IBLB_EINVAL, std::string("cannot open: ") + path);
+  StateHeader hd;
+  bool ok = fread(&hd, sizeof(hd), 1, fp) == 1 && memcmp(hd.magic, "IBLBST01", 8) == 0;
+  if (!ok || hd.nx != c.nx || hd.ny != c.ny || hd.nz != c.nz || hd.precision != c.precision ||
+      hd.has_walls != c.has_walls || hd.nv != c.nv || hd.nf != c.nf) {
+    fclose(fp);
+    return fail(c, IBLB_EINVAL, "state file does not match this context");
+  }
+  const size_t fbytes = (size_t)iblb::Q * c.ncell * c.real_size;
+  std::vector<char> fbuf(fbytes);
+  std::vector<double> qbuf((size_t)3 * c.nv), qdbuf((size_t)3 * c.nv);
+  std::vector<char> refbuf((size_t)4 * c.nf * sizeof(double));
+  std::vector<int> fcs((size_t)3 * c.nf);
+  ok = fread(fbuf.data(), 1, fbytes, fp) == fbytes;
+  if (c.nv) {
+    ok = ok && fread(qbuf.data(), sizeof(double), qbuf.size(), fp) == qbuf.size();
+    ok = ok && fread(qdbuf.data(), sizeof(double), qdbuf.size(), fp) == qdbuf.size();
+    ok = ok && fread(refbuf.data(), 1, refbuf.size(), fp) == refbuf.size();
+    ok = ok && fread(fcs.data(), sizeof(int), fcs.size(), fp) == fcs.size();
+  }
+  fclose(fp);
+  if (!ok) return fail(c, IBLB_EINVAL, "truncated state file");
+  if (c.nv) {
+    std::vector<int> mine((size_t)3 * c.nf);
+    CUDA_TRY(c, cudaMemcpy(mine.data(), c.faces, mine.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    if (mine != fcs) return fail(c, IBLB_EINVAL, "state file has a different face list");
+  }
+  c.tau = hd.tau; c.rho0 = hd.rho0;
+  for (int k = 0; k < 3; k++) { c.ub[k] = hd.ub[k]; c.ut[k] = hd.ut[k]; c.g[k] = hd.g[k]; }
+  c.fresh = hd.fresh;
+  c.steps_done = hd.steps_done;
+  CUDA_TRY(c, cudaMemcpyAsync(c.f[c.cur], fbuf.data(), fbytes, cudaMemcpyHostToDevice, c.stream));
+  if (c.nv) {
+    c.V0 = hd.V0;
+    for (int k = 0; k < 3; k++) c.centre[k] = hd.centre[k];
+    c.iface = hd.iface;
+    CUDA_TRY(c, cudaMemcpyAsync(c.q, qbuf.data(), qbuf.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c.qdot, qdbuf.data(), qdbuf.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c.fref, refbuf.data(), refbuf.size(), cudaMemcpyHostToDevice, c.stream));
+    c.have_force = 0;
+    if (int rc = remark(c, c.map)) return rc;
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  return IBLB_OK;
+}
+
+int64_t iblb_steps_done(const iblb_ctx *h) { return h ? h->c.steps_done : -1; }
+
+int iblb_set_profiling(iblb_ctx *h, int32_t on) {
+  if (!h) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  c.profiling = on ? 1 : 0;
+  c.ev_used = 0;
+  c.k1_launches = 0;
+  c.kernel_launches = 0;
+  return IBLB_OK;
+}
+
+int iblb_profile(iblb_ctx *h, double *k1_ms, int64_t *k1_launches, int64_t *kernel_launches) {
+  if (!h || !k1_ms || !k1_launches || !kernel_launches) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  double total = 0.0;
+  for (size_t k = 0; k + 1 < c.ev_used; k += 2) {
+    float ms = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&ms, c.ev_pool[k], c.ev_pool[k + 1]));
+    total += ms;
+  }
+  *k1_ms = total;
+  *k1_launches = c.k1_launches;
+  *kernel_launches = c.kernel_launches;
+  return IBLB_OK;
+}
+
+int64_t iblb_bytes_per_cell(const iblb_ctx *h) {
+  return h ? (int64_t)(2 * iblb::Q * h->c.real_size) : -1;
+}
+
+}  // extern "C"

@@ -1,0 +1,718 @@
+// Interface kernels: per-face forces (Eqs. 2, 17-19) with the double-precision volume sum,
+// per-vertex gathering into nodal forces (Eq. 16) and binning by 4x4x4 source tile,
+// spreading by owner-computes gather over the binned vertices (Eq. 13), interpolation and
+// the Euler update (Eqs. 11-12), and the marking of active tiles for the next step.
+//
+// Arithmetic runs in the population type `real` (float or double); vertex positions, the
+// enclosed volume V and V - V0 are always double.
+#include <math.h>
+
+#include "iblb_internal.cuh"
+
+namespace iblb {
+namespace {
+
+struct Dims {
+  int nx, ny, nz, has_walls, ntx, nty, ntz, max_slots;
+  double zb, zt;  // wall planes
+};
+
+Dims dims_of(const Ctx &c) {
+  Dims d;
+  d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.has_walls = c.has_walls;
+  d.ntx = c.ntx; d.nty = c.nty; d.ntz = c.ntz; d.max_slots = c.max_slots;
+  d.zb = 0.5;
+  d.zt = c.nz - 1.5;
+  return d;
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ int floor_div4(int a) { return a >= 0 ? a >> 2 : -((3 - a) >> 2); }
+
+__device__ __forceinline__ float log_(float v) { return logf(v); }
+__device__ __forceinline__ double log_(double v) { return log(v); }
+__device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
+__device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
+
+// Lennard-Jones force along z on a centroid at height gz above the wall plane zw (Eq. 19;
+// d points from the wall foot point to the centroid).
+template <typename real>
+__device__ __forceinline__ real lj_fz(double gz, double zw, real eps48, real xi) {
+  const real dz = (real)(gz - zw);
+  const real inv_d2 = real(1) / (dz * dz);
+  const real s2 = xi * xi * inv_d2;
+  const real s6 = s2 * s2 * s2;
+  return eps48 * (s6 * s6 - real(0.5) * s6) * dz * inv_d2;
+}
+
+struct FaceParams {
+  double a1, a2, a3;  // alpha
+  double eps48, xi;
+  int wall_on;
+  double cx, cy, cz;  // fixed point of the volume decomposition
+};
+
+// K3a: one thread per face. Writes the strain + wall force of each corner, the face's
+// volume gradient (a x b)/6, and one partial volume per block (summed in double, warp
+// shuffles in a fixed order).
+// With reset != 0 it also clears the tile map that the previous step used.
+template <typename real>
+__global__ void __launch_bounds__(256) face_kernel(
+    int nf, const int *__restrict__ faces, const double *__restrict__ q,
+    const double *__restrict__ fref, real *__restrict__ fcontrib, real *__restrict__ fnorm,
+    double *__restrict__ vol_partial, FaceParams fp, Dims D, int *__restrict__ other_tile_slot,
+    const int *__restrict__ other_slot_tile, const int *__restrict__ other_nslots, int reset,
+    int *__restrict__ ovf_count) {
+  __shared__ double warp_sum[8];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double vj = 0.0;
+  if (j < nf) {
+    const int i0 = faces[3 * j], i1 = faces[3 * j + 1], i2 = faces[3 * j + 2];
+    const double x0[3] = {q[3 * i0], q[3 * i0 + 1], q[3 * i0 + 2]};
+    const double x1[3] = {q[3 * i1], q[3 * i1 + 1], q[3 * i1 + 2]};
+    const double x2[3] = {q[3 * i2], q[3 * i2 + 1], q[3 * i2 + 2]};
+    double ad[3], bd[3];
+    real a[3], b[3];
+    for (int k = 0; k < 3; k++) {
+      ad[k] = x1[k] - x0[k];
+      bd[k] = x2[k] - x0[k];
+      a[k] = (real)ad[k];
+      b[k] = (real)bd[k];
+    }
+    const real H11 = (real)fref[4 * j], H12 = (real)fref[4 * j + 1], H22 = (real)fref[4 * j + 2],
+               A0 = (real)fref[4 * j + 3];
+    const real G11 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    const real G12 = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    const real G22 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const real detG = G11 * G22 - G12 * G12;
+    const real L = log_(detG / (real(4) * A0 * A0));  // log(I2 + 1), det G0 = 4 A0^2
+    const real dE_dI1 = real(0.5) * (real)fp.a3 * A0;
+    const real dE_dL = A0 * ((real)(0.5 * (fp.a1 - fp.a3)) + (real)(0.25 * (fp.a1 + fp.a2)) * L);
+    const real inv_detG = real(1) / detG;
+    real f0[3], f1[3], f2[3];
+    for (int k = 0; k < 3; k++) {
+      // dE/da and dE/db with I1 = H11 G11 + 2 H12 G12 + H22 G22 - 2, L = log det G + const
+      const real ga = dE_dI1 * real(2) * (H11 * a[k] + H12 * b[k]) +
+                      dE_dL * real(2) * (a[k] * G22 - G12 * b[k]) * inv_detG;
+      const real gb = dE_dI1 * real(2) * (H12 * a[k] + H22 * b[k]) +
+                      dE_dL * real(2) * (b[k] * G11 - G12 * a[k]) * inv_detG;
+      f1[k] = -ga;
+      f2[k] = -gb;
+      f0[k] = ga + gb;
+    }
+    if (fp.wall_on && D.has_walls) {
+      const double gz = (x0[2] + x1[2] + x2[2]) * (1.0 / 3.0);
+      const real third = (lj_fz<real>(gz, D.zb, (real)fp.eps48, (real)fp.xi) +
+                          lj_fz<real>(gz, D.zt, (real)fp.eps48, (real)fp.xi)) *
+                         real(1.0 / 3.0);
+      f0[2] += third;
+      f1[2] += third;
+      f2[2] += third;
+    }
+    real *fc = fcontrib + 9 * (size_t)j;
+    for (int k = 0; k < 3; k++) {
+      fc[k] = f0[k];
+      fc[3 + k] = f1[k];
+      fc[6 + k] = f2[k];
+    }
+    // Volume share of the face, V_j = (x0 - c).(x1 - c) x (x2 - c) / 6 = (x0 - c).(a x b) / 6,
+    // and its gradient. For a closed surface the gradient of V at vertex i does not depend
+    // on the point c, so taking c = x_i for the faces around i gives dV/dq_i = sum (a x b)/6:
+    // the same edge cross product for all three corners, free of the R^2 cancellation of
+    // products of position vectors.
+    const double n0 = ad[1] * bd[2] - ad[2] * bd[1];
+    const double n1 = ad[2] * bd[0] - ad[0] * bd[2];
+    const double n2 = ad[0] * bd[1] - ad[1] * bd[0];
+    vj = ((x0[0] - fp.cx) * n0 + (x0[1] - fp.cy) * n1 + (x0[2] - fp.cz) * n2) * (1.0 / 6.0);
+    real *fn = fnorm + 3 * (size_t)j;
+    fn[0] = (real)(n0 * (1.0 / 6.0));
+    fn[1] = (real)(n1 * (1.0 / 6.0));
+    fn[2] = (real)(n2 * (1.0 / 6.0));
+  }
+  // block sum of the face volumes, fixed shuffle tree
+  for (int o = 16; o > 0; o >>= 1) vj += __shfl_down_sync(0xffffffffu, vj, o);
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = vj;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? warp_sum[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) vol_partial[blockIdx.x] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ovf_count = 0;
+  if (reset) {
+    const int n_other = min(*other_nslots, D.max_slots);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_other; s += gridDim.x * blockDim.x)
+      other_tile_slot[other_slot_tile[s]] = -1;
+  }
+}
+
+// Sum of the per-block partial volumes in a fixed order by one warp.
+__device__ __forceinline__ double total_volume(const double *__restrict__ part, int n) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += 32) v += part[k];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// One-dimensional Peskin weights of the four nodes floor(p)-1 .. floor(p)+2 (Eq. 15).
+// With r = p - floor(p) and s = sqrt(1 + 4r - 4r^2) the four branches reduce to
+// (3-2r-s)/8, (3-2r+s)/8, (1+2r+s)/8, (1+2r-s)/8, which sum to one.
+template <typename real>
+__device__ __forceinline__ void peskin_weights(double p, int &base, real w[4]) {
+  const double fl = floor(p);
+  base = (int)fl - 1;
+  const real r = (real)(p - fl);
+  const real s = sqrt_(real(1) + real(4) * r - real(4) * r * r);
+  w[0] = (real(3) - real(2) * r - s) * real(0.125);
+  w[1] = (real(3) - real(2) * r + s) * real(0.125);
+  w[2] = (real(1) + real(2) * r + s) * real(0.125);
+  w[3] = (real(1) + real(2) * r - s) * real(0.125);
+}
+
+struct VertexParams {
+  double V0, kV;
+  int volume_on, vol_blocks;
+};
+
+// K3b: one thread per vertex. Nodal force (Eq. 16) = gathered corner forces minus
+// kV (V - V0)/V0 dV/dq (dV/dq = sum of the face gradients around the vertex), in face order; then the delta stencil of the vertex and its
+// binning into the source tile (the tile that holds its base node).
+template <typename real>
+__global__ void __launch_bounds__(256) vertex_kernel(
+    int nv, const double *__restrict__ vol_partial, VertexParams vp,
+    const int *__restrict__ vf_start, const int *__restrict__ vf_list,
+    const real *__restrict__ fcontrib, const real *__restrict__ fnorm,
+    const double *__restrict__ q, real *__restrict__ phi, StencilRec<real> *__restrict__ stencil,
+    int bin, const int *__restrict__ tile_slot, int *__restrict__ slot_count,
+    int *__restrict__ bucket, int *__restrict__ overflow, int *__restrict__ ovf_count,
+    int *__restrict__ health, int *__restrict__ zero_counter, Dims D) {
+  __shared__ double s_coef;
+  if (threadIdx.x < 32) {
+    const double V = total_volume(vol_partial, vp.vol_blocks);
+    if (threadIdx.x == 0) {
+      const double rel = (V - vp.V0) / vp.V0;
+      s_coef = vp.volume_on ? vp.kV * rel : 0.0;
+      if (blockIdx.x == 0) {
+        if (!(fabs(rel) <= 0.05)) atomicOr(health, H_VOLUME);
+        if (zero_counter) *zero_counter = 0;
+      }
+    }
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv) return;
+  const real coef = (real)s_coef;
+  real F[3] = {0, 0, 0};
+  const int e0 = vf_start[i], e1 = vf_start[i + 1];
+  for (int e = e0; e < e1; e++) {
+    const int fc = vf_list[e];  // face * 3 + corner
+    const int f = fc / 3;
+    for (int k = 0; k < 3; k++) F[k] += fcontrib[3 * (size_t)fc + k] - coef * fnorm[3 * (size_t)f + k];
+  }
+  for (int k = 0; k < 3; k++) phi[3 * (size_t)i + k] = F[k];
+  if (!bin) return;
+  StencilRec<real> rec;
+  for (int k = 0; k < 3; k++) peskin_weights<real>(q[3 * (size_t)i + k], rec.base[k], rec.w[k]);
+  rec.base[0] = wrapi(rec.base[0], D.nx);
+  rec.base[1] = wrapi(rec.base[1], D.ny);
+  if (!D.has_walls) rec.base[2] = wrapi(rec.base[2], D.nz);
+  rec.pad = 0;
+  stencil[i] = rec;
+  const int bz = min(max(rec.base[2], 0), D.nz - 1);
+  const int t = ((bz >> 2) * D.nty + (rec.base[1] >> 2)) * D.ntx + (rec.base[0] >> 2);
+  const int s = tile_slot[t];
+  if (s < 0) {
+    atomicOr(health, H_CAPACITY);
+    return;
+  }
+  const int rank = atomicAdd(&slot_count[s], 1);
+  if (rank < BUCKET_CAP) {
+    bucket[(size_t)s * BUCKET_CAP + rank] = i;
+  } else {
+    const int o = atomicAdd(ovf_count, 1);
+    overflow[o] = i;
+  }
+}
+
+// K4a: sort every source bucket of the current map by vertex index (one warp per bucket,
+// rank by comparison; bucket sizes are at most 64), so that spreading sums in an order that
+// does not depend on the order in which the vertex kernel filled the buckets.
+__global__ void __launch_bounds__(256) sort_buckets_kernel(const int *__restrict__ nslots_ptr,
+                                                           const int *__restrict__ slot_count,
+                                                           int *__restrict__ bucket, int max_slots) {
+  const int nslots = min(*nslots_ptr, max_slots);
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nslots; s += warps) {
+    const int n = min(slot_count[s], BUCKET_CAP);
+    int *bk = bucket + (size_t)s * BUCKET_CAP;
+    const int v0 = lane < n ? bk[lane] : 0x7fffffff;
+    const int v1 = lane + 32 < n ? bk[lane + 32] : 0x7fffffff;
+    int r0 = 0, r1 = 0;
+    for (int m = 0; m < n; m++) {
+      const int vm = __shfl_sync(0xffffffffu, m < 32 ? v0 : v1, m & 31);
+      r0 += vm < v0;
+      r1 += vm < v1;
+    }
+    __syncwarp();
+    if (lane < n) bk[r0] = v0;
+    if (lane + 32 < n) bk[r1] = v1;
+  }
+}
+
+// Candidates staged per tile and pass of the spreading kernel.
+constexpr int SPREAD_CHUNK = 64;
+// Active tiles per 64-thread spreading block (16 threads per tile).
+constexpr int SPREAD_TILES = 4;
+
+// K4b: spreading (Eq. 13). A 64-thread block handles 4 active tiles; 16 threads per tile,
+// thread (ly, lz) owns the x-row of 4 nodes (0..3, ly, lz). The candidates of a tile are the
+// vertices binned in its eight source tiles T - {0,1}^3 (every vertex whose stencil reaches
+// T lies there), in bucket order, then the overflow list. When a candidate is staged its
+// one-dimensional weights are re-indexed to the tile's node coordinates, zero where the
+// stencil misses the tile, so the inner loop is a branch-free separable product. Each
+// thread writes its own nodes once: no atomics, and the summation order is fixed by the
+// sorted buckets (the overflow list, normally empty, follows arrival order).
+template <typename real>
+__global__ void __launch_bounds__(64) spread_kernel(
+    const int *__restrict__ tile_slot, const int *__restrict__ slot_tile,
+    const int *__restrict__ nslots_ptr, const int *__restrict__ slot_count,
+    const int *__restrict__ bucket, const int *__restrict__ overflow,
+    const int *__restrict__ ovf_count_ptr, const StencilRec<real> *__restrict__ stencil,
+    const real *__restrict__ phi, real *__restrict__ Fslot, Dims D) {
+  __shared__ int s_src_slot[SPREAD_TILES][8];
+  __shared__ int s_src_start[SPREAD_TILES][9];
+  __shared__ real s_wx[SPREAD_TILES][SPREAD_CHUNK][4];
+  __shared__ real s_wy[SPREAD_TILES][SPREAD_CHUNK][4];
+  __shared__ real s_wz[SPREAD_TILES][SPREAD_CHUNK][4];
+  __shared__ real s_phi[SPREAD_TILES][SPREAD_CHUNK][4];
+  const int nslots = min(*nslots_ptr, D.max_slots);
+  const int novf = *ovf_count_ptr;
+  const int tq = threadIdx.x >> 4;  // tile of this thread within the block
+  const int r = threadIdx.x & 15;
+  const int ly = r & 3, lz = r >> 2;
+  for (int b0 = blockIdx.x * SPREAD_TILES; b0 < nslots; b0 += gridDim.x * SPREAD_TILES) {
+    const int b = b0 + tq;
+    const bool active = b < nslots;
+    int tx = 0, ty = 0, tz = 0;
+    if (active) {
+      const int t = slot_tile[b];
+      tx = t % D.ntx;
+      ty = (t / D.ntx) % D.nty;
+      tz = t / (D.ntx * D.nty);
+    }
+    __syncthreads();  // shared arrays of the previous round are no longer read
+    if (r < 8) {
+      int slot = -1, count = 0;
+      if (active) {
+        int sx = tx - (r & 1), sy = ty - ((r >> 1) & 1), sz = tz - (r >> 2);
+        sx = sx < 0 ? sx + D.ntx : sx;
+        sy = sy < 0 ? sy + D.nty : sy;
+        bool ok = true;
+        if (sz < 0) {
+          if (D.has_walls) ok = false;
+          sz += D.ntz;
+        }
+        // with a single tile along an axis both offsets name the same tile
+        if (((r & 1) && D.ntx == 1) || (((r >> 1) & 1) && D.nty == 1) || ((r >> 2) && D.ntz == 1))
+          ok = false;
+        if (ok) {
+          slot = tile_slot[(sz * D.nty + sy) * D.ntx + sx];
+          if (slot >= 0) count = min(slot_count[slot], BUCKET_CAP);
+          else slot = -1;
+        }
+      }
+      s_src_slot[tq][r] = slot;
+      s_src_start[tq][r + 1] = count;
+    }
+    __syncthreads();
+    if (r == 0) {
+      s_src_start[tq][0] = 0;
+      for (int k = 1; k <= 8; k++) s_src_start[tq][k] += s_src_start[tq][k - 1];
+    }
+    __syncthreads();
+    const int nb = s_src_start[tq][8];
+    const int total = active ? nb + novf : 0;
+    // the block runs as many passes as its largest tile needs
+    int passes = (total + SPREAD_CHUNK - 1) / SPREAD_CHUNK;
+    for (int o = 16; o < 64; o <<= 1) passes = max(passes, __shfl_xor_sync(0xffffffffu, passes, o));
+    __shared__ int s_passes[2];
+    if ((threadIdx.x & 31) == 0) s_passes[threadIdx.x >> 5] = passes;
+    __syncthreads();
+    passes = max(s_passes[0], s_passes[1]);
+    const int X0 = tx * TILE, Y0 = ty * TILE, Z0 = tz * TILE;
+    real acc[4][3];
+    for (int i = 0; i < 4; i++) acc[i][0] = acc[i][1] = acc[i][2] = 0;
+    for (int p = 0; p < passes; p++) {
+      const int c0 = p * SPREAD_CHUNK;
+      const int nload = max(0, min(SPREAD_CHUNK, total - c0));
+      if (p > 0) __syncthreads();
+      for (int k = r; k < nload; k += 16) {
+        const int g = c0 + k;
+        int v;
+        if (g < nb) {
+          int src = 0;
+          while (g >= s_src_start[tq][src + 1]) src++;
+          v = bucket[(size_t)s_src_slot[tq][src] * BUCKET_CAP + (g - s_src_start[tq][src])];
+        } else {
+          v = overflow[g - nb];
+        }
+        const StencilRec<real> &rec = stencil[v];
+        for (int l = 0; l < 4; l++) {
+          int dx = X0 + l - rec.base[0];
+          dx = dx < 0 ? dx + D.nx : dx;
+          int dy = Y0 + l - rec.base[1];
+          dy = dy < 0 ? dy + D.ny : dy;
+          int dz = Z0 + l - rec.base[2];
+          if (!D.has_walls) dz = dz < 0 ? dz + D.nz : dz;
+          s_wx[tq][k][l] = dx < 4 ? rec.w[0][dx] : real(0);
+          s_wy[tq][k][l] = dy < 4 ? rec.w[1][dy] : real(0);
+          s_wz[tq][k][l] = (unsigned)dz < 4u ? rec.w[2][dz] : real(0);
+        }
+        s_phi[tq][k][0] = phi[3 * (size_t)v];
+        s_phi[tq][k][1] = phi[3 * (size_t)v + 1];
+        s_phi[tq][k][2] = phi[3 * (size_t)v + 2];
+      }
+      __syncthreads();
+      for (int k = 0; k < nload; k++) {
+        const real t = s_wy[tq][k][ly] * s_wz[tq][k][lz];
+        if (t == real(0)) continue;
+        const real g0 = t * s_phi[tq][k][0], g1 = t * s_phi[tq][k][1], g2 = t * s_phi[tq][k][2];
+        for (int l = 0; l < 4; l++) {
+          const real wx = s_wx[tq][k][l];
+          acc[l][0] += wx * g0;
+          acc[l][1] += wx * g1;
+          acc[l][2] += wx * g2;
+        }
+      }
+    }
+    if (active) {
+      // force landing on a wall layer is dropped
+      const int Z = Z0 + lz;
+      const bool drop = D.has_walls && (Z == 0 || Z >= D.nz - 1);
+      real *Fs = Fslot + (size_t)b * 3 * TILE_CELLS + 4 * ly + 16 * lz;
+      for (int l = 0; l < 4; l++)
+        for (int k = 0; k < 3; k++) Fs[k * TILE_CELLS + l] = drop ? real(0) : acc[l][k];
+    }
+  }
+}
+
+// Claim tile t in map (tile_slot, slot_tile, nslots): the first claimant takes a new slot.
+// A plain read first keeps the many vertices of an already-claimed tile off the atomic.
+__device__ __forceinline__ void claim_tile(int t, int *tile_slot, int *slot_tile, int *nslots,
+                                           int *slot_count, int *health, int max_slots) {
+  if (*(volatile int *)&tile_slot[t] != -1) return;
+  if (atomicCAS(&tile_slot[t], -1, -2) == -1) {
+    const int s = atomicAdd(nslots, 1);
+    if (s < max_slots) {
+      slot_tile[s] = t;
+      slot_count[s] = 0;
+      atomicExch(&tile_slot[t], s);
+    } else {
+      atomicOr(health, H_CAPACITY);
+    }
+  }
+}
+
+// Mark tile e (0..7: one bit per axis picks the lower or upper tile) covered by the stencil
+// of position p.
+__device__ __forceinline__ void mark_tiles(const double p[3], int e, const Dims &D,
+                                           int *tile_slot, int *slot_tile, int *nslots,
+                                           int *slot_count, int *health) {
+  int t[3];
+  const int n[3] = {D.nx, D.ny, D.nz};
+  const int nt[3] = {D.ntx, D.nty, D.ntz};
+  for (int k = 0; k < 3; k++) {
+    const int b = (int)floor(p[k]) - 1;
+    const int t0 = floor_div4(b), t1 = floor_div4(b + 3);
+    const int pick = (e >> k) & 1;
+    if (pick && t1 == t0) return;  // the stencil stays in one tile along this axis
+    int tk = pick ? t1 : t0;
+    if (k < 2 || !D.has_walls) {
+      tk %= nt[k];
+      if (tk < 0) tk += nt[k];
+      // the stencil of a short periodic axis may wrap onto the same tile twice
+      if (pick && tk == ((t0 % nt[k]) + nt[k]) % nt[k]) return;
+    } else if (tk < 0 || tk >= nt[k] || tk * TILE >= n[k]) {
+      return;  // beyond the lattice in z: those stencil nodes are skipped
+    }
+    t[k] = tk;
+  }
+  claim_tile((t[2] * D.nty + t[1]) * D.ntx + t[0], tile_slot, slot_tile, nslots, slot_count,
+             health, D.max_slots);
+}
+
+// K2: interpolation (Eq. 11) and the Euler update (Eq. 12); 4 lanes per vertex, lane dz
+// sums the 16 nodes of its z-plane of the stencil, the 4 planes are summed by shuffles and
+// the update is added to the double position. Each lane then marks two of the (up to 8)
+// tiles of the new position in the other map.
+template <typename real>
+__global__ void __launch_bounds__(256) interp_kernel(
+    int nv, const StencilRec<real> *__restrict__ stencil, const int *__restrict__ tile_slot,
+    const real *__restrict__ Uslot, double *__restrict__ q, double *__restrict__ qdot,
+    double3 ub, double3 ut, Dims D, int *__restrict__ next_tile_slot,
+    int *__restrict__ next_slot_tile, int *__restrict__ next_nslots, int *__restrict__ slot_count,
+    int *__restrict__ health) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = gid >> 2;
+  const int dz = gid & 3;
+  const bool valid = v < nv;
+  real acc[3] = {0, 0, 0};
+  if (valid) {
+    const StencilRec<real> &rec = stencil[v];
+    int Z = rec.base[2] + dz;
+    if (!D.has_walls) Z = Z >= D.nz ? Z - D.nz : Z;
+    if (Z >= 0 && Z < D.nz) {
+      const real wz = rec.w[2][dz];
+      if (D.has_walls && (Z == 0 || Z == D.nz - 1)) {
+        const double3 w = Z == 0 ? ub : ut;
+        const real sxy = (rec.w[0][0] + rec.w[0][1] + rec.w[0][2] + rec.w[0][3]) *
+                         (rec.w[1][0] + rec.w[1][1] + rec.w[1][2] + rec.w[1][3]) * wz;
+        acc[0] = sxy * (real)w.x;
+        acc[1] = sxy * (real)w.y;
+        acc[2] = sxy * (real)w.z;
+      } else {
+        // the 4 stencil nodes along x (and along y) fall in at most two tiles: look up the
+        // (up to) four tile slots of this z-plane once
+        int X[4], Y[4];
+        for (int d = 0; d < 4; d++) {
+          const int xx = rec.base[0] + d, yy = rec.base[1] + d;
+          X[d] = xx >= D.nx ? xx - D.nx : xx;
+          Y[d] = yy >= D.ny ? yy - D.ny : yy;
+        }
+        const int tzrow = (Z >> 2) * D.nty;
+        int sl[2][2];
+        for (int iy = 0; iy < 2; iy++)
+          for (int ix = 0; ix < 2; ix++)
+            sl[iy][ix] = tile_slot[(tzrow + (Y[3 * iy] >> 2)) * D.ntx + (X[3 * ix] >> 2)];
+        for (int dy = 0; dy < 4; dy++) {
+          const int iy = (Y[dy] >> 2) != (Y[0] >> 2);
+          const int crow = 4 * (Y[dy] & 3) + 16 * (Z & 3);
+          real r3[3] = {0, 0, 0};
+          for (int dx = 0; dx < 4; dx++) {
+            const int sidx = sl[iy][(X[dx] >> 2) != (X[0] >> 2)];
+            if (sidx < 0) {  // unmarked tile: only after a capacity failure, flagged there
+              atomicOr(health, H_CAPACITY);
+              continue;
+            }
+            const real *Us = Uslot + (size_t)sidx * 3 * TILE_CELLS + (X[dx] & 3) + crow;
+            const real w = rec.w[0][dx];
+            r3[0] += w * Us[0];
+            r3[1] += w * Us[TILE_CELLS];
+            r3[2] += w * Us[2 * TILE_CELLS];
+          }
+          const real wyz = rec.w[1][dy] * wz;
+          acc[0] += wyz * r3[0];
+          acc[1] += wyz * r3[1];
+          acc[2] += wyz * r3[2];
+        }
+      }
+    }
+  }
+  // sum of the 4 planes (fixed butterfly order)
+  for (int o = 2; o > 0; o >>= 1)
+    for (int k = 0; k < 3; k++) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  if (valid) {
+    double pn[3];
+    for (int k = 0; k < 3; k++) pn[k] = q[3 * (size_t)v + k] + (double)acc[k];
+    if (dz == 0) {
+      int h = 0;
+      for (int k = 0; k < 3; k++) {
+        qdot[3 * (size_t)v + k] = (double)acc[k];
+        q[3 * (size_t)v + k] = pn[k];
+        if (!(fabs((double)acc[k]) < 0.1)) h |= (acc[k] == acc[k]) ? H_FAST : H_NAN;
+      }
+      if (D.has_walls && (pn[2] - D.zb < 0.05 || D.zt - pn[2] < 0.05)) h |= H_WALL;
+      if (h) atomicOr(health, h);
+    }
+    if (next_tile_slot != nullptr && pn[0] == pn[0] && pn[1] == pn[1] && pn[2] == pn[2]) {
+      mark_tiles(pn, dz, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, health);
+      mark_tiles(pn, dz + 4, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, health);
+    }
+  }
+}
+
+// Standalone marking of the current positions (after setting vertices).
+__global__ void mark_kernel(int nv, const double *__restrict__ q, Dims D, int *tile_slot,
+                            int *slot_tile, int *nslots, int *slot_count, int *health) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = gid >> 3, e = gid & 7;
+  if (v >= nv) return;
+  const double p[3] = {q[3 * (size_t)v], q[3 * (size_t)v + 1], q[3 * (size_t)v + 2]};
+  if (p[0] == p[0] && p[1] == p[1] && p[2] == p[2])
+    mark_tiles(p, e, D, tile_slot, slot_tile, nslots, slot_count, health);
+}
+
+__global__ void clear_counts_kernel(const int *__restrict__ nslots, int *__restrict__ slot_count,
+                                    int *__restrict__ ovf_count, int max_slots) {
+  const int n = min(*nslots, max_slots);
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+    slot_count[s] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ovf_count = 0;
+}
+
+template <typename real>
+__global__ void expand_force_kernel(const int *__restrict__ slot_tile, const int *__restrict__ nslots,
+                                    const real *__restrict__ Fslot, Dims D, double *__restrict__ F) {
+  const int n = min(*nslots, D.max_slots);
+  for (int b = blockIdx.x; b < n; b += gridDim.x) {
+    const int t = slot_tile[b];
+    const int tx = t % D.ntx, ty = (t / D.ntx) % D.nty, tz = t / (D.ntx * D.nty);
+    const int c = threadIdx.x;
+    const int X = tx * TILE + (c & 3), Y = ty * TILE + ((c >> 2) & 3), Z = tz * TILE + (c >> 4);
+    if (Z >= D.nz) continue;
+    const size_t node = ((size_t)Z * D.ny + Y) * D.nx + X;
+    for (int k = 0; k < 3; k++)
+      F[3 * node + k] = (double)Fslot[(size_t)b * 3 * TILE_CELLS + k * TILE_CELLS + c];
+  }
+}
+
+template <typename real>
+__global__ void to_double_kernel(int n, const real *__restrict__ in, double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+
+__global__ void volume_sum_kernel(const double *__restrict__ part, int n, double *__restrict__ out) {
+  const double v = total_volume(part, n);
+  if (threadIdx.x == 0) *out = v;
+}
+
+template <typename real>
+cudaError_t face_forces_t(Ctx &c, int reset, cudaStream_t st) {
+  FaceParams fp;
+  fp.a1 = c.iface.alpha[0];
+  fp.a2 = c.iface.alpha[1];
+  fp.a3 = c.iface.alpha[2];
+  fp.eps48 = 48.0 * c.iface.eps;
+  fp.xi = c.iface.xi;
+  fp.wall_on = c.iface.wall_force_on;
+  fp.cx = c.centre[0];
+  fp.cy = c.centre[1];
+  fp.cz = c.centre[2];
+  const int other = c.map ^ 1;
+  face_kernel<real><<<c.vol_blocks, 256, 0, st>>>(
+      c.nf, c.faces, c.q, c.fref, (real *)c.fcontrib, (real *)c.fnorm, c.vol_partial, fp,
+      dims_of(c), c.tile_slot[other], c.slot_tile[other], c.counters + other, reset,
+      c.counters + 2);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t vertex_forces_t(Ctx &c, int bin, cudaStream_t st) {
+  VertexParams vp;
+  vp.V0 = c.V0;
+  vp.kV = c.iface.kV;
+  vp.volume_on = c.iface.volume_force_on;
+  vp.vol_blocks = c.vol_blocks;
+  vertex_kernel<real><<<(c.nv + 255) / 256, 256, 0, st>>>(
+      c.nv, c.vol_partial, vp, c.vf_start, c.vf_list, (const real *)c.fcontrib,
+      (const real *)c.fnorm, c.q, (real *)c.phi, (StencilRec<real> *)c.stencil, bin,
+      c.tile_slot[c.map], c.slot_count, c.bucket, c.overflow, c.counters + 2, c.counters + 3,
+      bin == 2 ? c.counters + (c.map ^ 1) : nullptr, dims_of(c));
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t spread_t(Ctx &c, cudaStream_t st) {
+  int sgrid = c.sm_count * 8;
+  if (sgrid * 8 > c.max_slots) sgrid = (c.max_slots + 7) / 8;
+  sort_buckets_kernel<<<sgrid, 256, 0, st>>>(c.counters + c.map, c.slot_count, c.bucket, c.max_slots);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int grid = c.sm_count * 16;
+  if (grid * SPREAD_TILES > c.max_slots) grid = (c.max_slots + SPREAD_TILES - 1) / SPREAD_TILES;
+  if (grid < 1) grid = 1;
+  spread_kernel<real><<<grid, TILE_CELLS, 0, st>>>(
+      c.tile_slot[c.map], c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.bucket,
+      c.overflow, c.counters + 2, (const StencilRec<real> *)c.stencil, (const real *)c.phi,
+      (real *)c.Fslot[c.map], dims_of(c));
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t interp_t(Ctx &c, cudaStream_t st) {
+  const int other = c.map ^ 1;
+  const long threads = 4L * c.nv;
+  interp_kernel<real><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      c.nv, (const StencilRec<real> *)c.stencil, c.tile_slot[c.map], (const real *)c.Uslot, c.q,
+      c.qdot, make_double3(c.ub[0], c.ub[1], c.ub[2]), make_double3(c.ut[0], c.ut[1], c.ut[2]),
+      dims_of(c), c.tile_slot[other], c.slot_tile[other], c.counters + other, c.slot_count,
+      c.counters + 3);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t stencil_record_bytes(const Ctx &c) {
+  return c.precision == IBLB_FP64 ? sizeof(StencilRec<double>) : sizeof(StencilRec<float>);
+}
+
+cudaError_t launch_face_forces(Ctx &c, int reset_other_map, cudaStream_t s) {
+  return c.precision == IBLB_FP64 ? face_forces_t<double>(c, reset_other_map, s)
+                                  : face_forces_t<float>(c, reset_other_map, s);
+}
+
+// bin: 0 forces only; 1 forces + stencil + binning; 2 as 1 and also zero the other map's
+// tile counter (inside a step, after that map was cleared by the face kernel).
+cudaError_t launch_vertex_forces(Ctx &c, int bin, cudaStream_t s) {
+  return c.precision == IBLB_FP64 ? vertex_forces_t<double>(c, bin, s)
+                                  : vertex_forces_t<float>(c, bin, s);
+}
+
+cudaError_t launch_spread(Ctx &c, cudaStream_t s) {
+  return c.precision == IBLB_FP64 ? spread_t<double>(c, s) : spread_t<float>(c, s);
+}
+
+cudaError_t launch_interpolate_advect(Ctx &c, cudaStream_t s) {
+  return c.precision == IBLB_FP64 ? interp_t<double>(c, s) : interp_t<float>(c, s);
+}
+
+cudaError_t launch_mark(Ctx &c) {
+  const long threads = 8L * c.nv;
+  mark_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.stream>>>(
+      c.nv, c.q, dims_of(c), c.tile_slot[c.map], c.slot_tile[c.map], c.counters + c.map,
+      c.slot_count, c.counters + 3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clear_counts(Ctx &c) {
+  int grid = (c.max_slots + 255) / 256;
+  if (grid > 1024) grid = 1024;
+  clear_counts_kernel<<<grid, 256, 0, c.stream>>>(c.counters + c.map, c.slot_count, c.counters + 2,
+                                                  c.max_slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_force(Ctx &c, double *F_dev) {
+  int grid = c.sm_count * 8;
+  if (grid > c.max_slots) grid = c.max_slots;
+  if (grid < 1) grid = 1;
+  if (c.precision == IBLB_FP64)
+    expand_force_kernel<double><<<grid, TILE_CELLS, 0, c.stream>>>(
+        c.slot_tile[c.map], c.counters + c.map, (const double *)c.Fslot[c.map], dims_of(c), F_dev);
+  else
+    expand_force_kernel<float><<<grid, TILE_CELLS, 0, c.stream>>>(
+        c.slot_tile[c.map], c.counters + c.map, (const float *)c.Fslot[c.map], dims_of(c), F_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi_to_double(Ctx &c, double *phi_dev) {
+  const int n = 3 * c.nv;
+  if (c.precision == IBLB_FP64)
+    to_double_kernel<double><<<(n + 255) / 256, 256, 0, c.stream>>>(n, (const double *)c.phi, phi_dev);
+  else
+    to_double_kernel<float><<<(n + 255) / 256, 256, 0, c.stream>>>(n, (const float *)c.phi, phi_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_volume(Ctx &c, double *V_dev) {
+  volume_sum_kernel<<<1, 32, 0, c.stream>>>(c.vol_partial, c.vol_blocks, V_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace iblb

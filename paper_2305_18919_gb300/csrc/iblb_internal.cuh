@@ -1,0 +1,136 @@
+// Internal declarations of the IB-LB CUDA library: the context, device constants of the
+// D3Q19 lattice and the launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/iblb.h"
+
+namespace iblb {
+
+// ---------------------------------------------------------------------------------------
+// D3Q19 (Sec. III): 0 rest, 1..6 axis, 7..18 edge diagonals; opposite pairs (2k-1, 2k).
+// ---------------------------------------------------------------------------------------
+constexpr int Q = 19;
+__host__ __device__ constexpr int cx(int i) {
+  constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+  return t[i];
+}
+__host__ __device__ constexpr int cy(int i) {
+  constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+  return t[i];
+}
+__host__ __device__ constexpr int cz(int i) {
+  constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+  return t[i];
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// weights 1/3, 1/18, 1/36 (Sec. III footnote)
+__host__ __device__ constexpr double wgt(int i) {
+  return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Interface tiles: the lattice is cut into 4x4x4 tiles; only tiles touched by a vertex's
+// 4x4x4 delta stencil ("active" tiles) carry force and velocity buffers.
+constexpr int TILE = 4;
+constexpr int TILE_CELLS = TILE * TILE * TILE;
+// vertices per source-tile bucket before they spill to the overflow list
+constexpr int BUCKET_CAP = 64;
+
+// Health word bits (read back by iblb_step).
+constexpr int H_NAN = 1, H_FAST = 2, H_WALL = 4, H_VOLUME = 8, H_CAPACITY = 16;
+
+// Per-vertex stencil record written by the vertex kernel and read by spreading and
+// interpolation: base node (floor(q) - 1, x/y wrapped), the 3x4 one-dimensional weights.
+template <typename real>
+struct StencilRec {
+  int base[3];
+  int pad;
+  real w[3][4];
+};
+
+struct Ctx {
+  // lattice
+  int nx = 0, ny = 0, nz = 0, precision = 0, has_walls = 1;
+  double tau = 1.0, rho0 = 1.0, ub[3] = {0, 0, 0}, ut[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+  size_t ncell = 0;
+  size_t real_size = 4;
+  void *f[2] = {nullptr, nullptr};  // populations f_i - w_i rho0, [19][nz][ny][nx]
+  int cur = 0;                      // f[cur] holds the state
+  int fresh = 1;                    // state is post-streaming (no collision done yet)
+  int have_force = 0;               // a spread field exists (for read_fields)
+  cudaStream_t stream = nullptr;   // caller's stream: lattice kernels and all transfers
+  cudaStream_t ib = nullptr;       // library stream: the interface chain of each step
+  cudaEvent_t ev_force = nullptr;  // spread force of the step is ready (recorded on ib)
+  cudaEvent_t ev_coll = nullptr;   // post-collision populations of the step are complete
+  cudaEvent_t ev_sync = nullptr;   // general cross-stream join
+  // tiles
+  int ntx = 0, nty = 0, ntz = 0;
+  size_t ntiles = 0;
+  int max_slots = 0;
+  int *tile_slot[2] = {nullptr, nullptr};  // [ntiles] slot or -1
+  int *slot_tile[2] = {nullptr, nullptr};  // [max_slots] tile id of each active slot
+  int *counters = nullptr;                 // [0..1] nslots per map, [2] overflow count, [3] health
+  int *slot_count = nullptr;               // [max_slots] vertices in each source bucket
+  int *bucket = nullptr;                   // [max_slots][BUCKET_CAP]
+  int *overflow = nullptr;                 // [nv] vertices not fitting in their bucket
+  void *Fslot[2] = {nullptr, nullptr};     // per map: [max_slots][3][64] force density
+  void *Uslot = nullptr;                   // [max_slots][3][64] velocity
+  int map = 0;                             // tile map of the current vertex positions
+  // mesh
+  int nv = 0, nf = 0;
+  double *q = nullptr;       // [nv][3] positions (double in every precision)
+  double *qdot = nullptr;    // [nv][3]
+  int *faces = nullptr;      // [nf][3]
+  double *fref = nullptr;    // [nf][4] reference metric inverse (H11, H12, H22) and A0
+  int *vf_start = nullptr;   // [nv+1] CSR vertex -> (face*3 + corner)
+  int *vf_list = nullptr;    // [3 nf]
+  void *fcontrib = nullptr;  // [nf][3 corners][3]: strain + wall force per corner
+  void *fnorm = nullptr;     // [nf][3]: (a x b)/6, the face's volume gradient at each corner
+  double *vol_partial = nullptr;  // [vol_blocks]
+  int vol_blocks = 0;
+  void *phi = nullptr;       // [nv][3] nodal forces of the last evaluation
+  void *stencil = nullptr;   // [nv] StencilRec
+  double V0 = 0.0, centre[3] = {0, 0, 0};
+  iblb_iface_params iface{};
+  // bookkeeping
+  int64_t steps_done = 0;
+  int profiling = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  int64_t k1_launches = 0, kernel_launches = 0;
+  std::vector<cudaEvent_t> ev_near;  // events around the active-tile collision (profiling)
+  size_t ev_near_used = 0;
+  double *dscratch = nullptr;  // host-transfer staging buffer (doubles)
+  size_t dscratch_len = 0;
+  int sm_count = 0;
+  std::string err;
+};
+
+// Launchers (each returns cudaGetLastError() of its launch) on stream `s`.
+// Stream-collide of every fluid node with the body force only (no interface force).
+cudaError_t launch_stream_collide(Ctx &c, int first, cudaStream_t s);
+// Stream-collide again of the nodes of the active tiles, with the interface force.
+cudaError_t launch_stream_collide_tiles(Ctx &c, int first, cudaStream_t s);
+cudaError_t launch_shell_velocity(Ctx &c, cudaStream_t s);
+cudaError_t launch_fields(Ctx &c, double *rho_dev, double *u_dev);
+cudaError_t launch_populations(Ctx &c, double *f_dev);
+cudaError_t launch_init_equilibrium(Ctx &c, const double *rho_dev, const double *u_dev);
+
+cudaError_t launch_face_forces(Ctx &c, int reset_other_map, cudaStream_t s);
+// Device bytes of one stencil record in the context's precision.
+size_t stencil_record_bytes(const Ctx &c);
+cudaError_t launch_vertex_forces(Ctx &c, int bin, cudaStream_t s);
+cudaError_t launch_spread(Ctx &c, cudaStream_t s);
+cudaError_t launch_interpolate_advect(Ctx &c, cudaStream_t s);
+cudaError_t launch_mark(Ctx &c);
+cudaError_t launch_clear_counts(Ctx &c);
+cudaError_t launch_expand_force(Ctx &c, double *F_dev);
+cudaError_t launch_phi_to_double(Ctx &c, double *phi_dev);
+cudaError_t launch_volume(Ctx &c, double *V_dev);
+
+}  // namespace iblb

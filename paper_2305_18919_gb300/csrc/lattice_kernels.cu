@@ -1,0 +1,420 @@
+// Lattice-Boltzmann kernels: the fused pull stream-collide over the whole lattice (Eqs. 9-10
+// with Guo forcing and half-way bounce-back), the velocity gather at the active interface
+// tiles (the velocity step of Sec. III), and the read-back / initialisation helpers.
+//
+// Populations are stored as deviations f_i - w_i rho0 ("shifted"), structure of arrays
+// [19][nz][ny][nx] with x fastest. The state array holds post-collision populations of
+// the previous step; a pull reads f_i(x - c_i) from it, which is the streaming step.
+// Right after initialisation the state holds post-streaming populations ("fresh") and the
+// first collision reads them in place.
+#include "iblb_internal.cuh"
+
+namespace iblb {
+namespace {
+
+template <typename real>
+struct LatParams {
+  int nx, ny, nz, has_walls;
+  int ntx, nty;
+  size_t ncell;
+  real omega;        // 1/tau
+  real guo;          // 1 - 1/(2 tau)
+  real rho0;
+  real g[3];         // uniform body force
+  real wb[19];       // 6 w_i rho0 (c_i . u_bottom): moving-wall term, bottom wall
+  real wt[19];       // same for the top wall
+};
+
+template <typename real>
+LatParams<real> lat_params(const Ctx &c) {
+  LatParams<real> p;
+  p.nx = c.nx; p.ny = c.ny; p.nz = c.nz; p.has_walls = c.has_walls;
+  p.ntx = c.ntx; p.nty = c.nty;
+  p.ncell = c.ncell;
+  p.omega = (real)(1.0 / c.tau);
+  p.guo = (real)(1.0 - 0.5 / c.tau);
+  p.rho0 = (real)c.rho0;
+  for (int k = 0; k < 3; k++) p.g[k] = (real)c.g[k];
+  for (int i = 0; i < Q; i++) {
+    double cb = cx(i) * c.ub[0] + cy(i) * c.ub[1] + cz(i) * c.ub[2];
+    double ct = cx(i) * c.ut[0] + cy(i) * c.ut[1] + cz(i) * c.ut[2];
+    p.wb[i] = (real)(6.0 * wgt(i) * c.rho0 * cb);
+    p.wt[i] = (real)(6.0 * wgt(i) * c.rho0 * ct);
+  }
+  return p;
+}
+
+// Pull the 19 post-streaming populations of fluid node (x, y, z) from post-collision array
+// `fp`. A link whose source is a wall node is bounced back: the opposite post-collision
+// population of the same node plus the moving-wall term.
+template <typename real>
+__device__ __forceinline__ void pull(const real *__restrict__ fp, const LatParams<real> &P, int x,
+                                     int y, int z, real f[Q]) {
+  const int xm = x == 0 ? P.nx - 1 : x - 1, xp = x == P.nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
+  int zm = z - 1, zp = z + 1;
+  if (!P.has_walls) {
+    zm = z == 0 ? P.nz - 1 : zm;
+    zp = z == P.nz - 1 ? 0 : zp;
+  }
+  const bool wall_below = P.has_walls && zm == 0;
+  const bool wall_above = P.has_walls && zp == P.nz - 1;
+  const size_t n = ((size_t)z * P.ny + y) * P.nx + x;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const int sx = cx(i) > 0 ? xm : (cx(i) < 0 ? xp : x);
+    const int sy = cy(i) > 0 ? ym : (cy(i) < 0 ? yp : y);
+    const int sz = cz(i) > 0 ? zm : (cz(i) < 0 ? zp : z);
+    if (cz(i) > 0 && wall_below) {
+      f[i] = fp[(size_t)opp(i) * P.ncell + n] + P.wb[i];
+    } else if (cz(i) < 0 && wall_above) {
+      f[i] = fp[(size_t)opp(i) * P.ncell + n] + P.wt[i];
+    } else {
+      f[i] = fp[(size_t)i * P.ncell + ((size_t)sz * P.ny + sy) * P.nx + sx];
+    }
+  }
+}
+
+// Interface force density of node (x, y, z) from the active-tile table (0 if inactive).
+template <typename real>
+__device__ __forceinline__ void tile_force(const int *__restrict__ tile_slot,
+                                           const real *__restrict__ Fslot,
+                                           const LatParams<real> &P, int x, int y, int z,
+                                           real F[3]) {
+  F[0] = P.g[0];
+  F[1] = P.g[1];
+  F[2] = P.g[2];
+  if (tile_slot == nullptr) return;
+  const int t = ((z >> 2) * P.nty + (y >> 2)) * P.ntx + (x >> 2);
+  const int s = tile_slot[t];
+  if (s >= 0) {
+    const int cell = (x & 3) + 4 * (y & 3) + 16 * (z & 3);
+    const real *Fs = Fslot + (size_t)s * 3 * TILE_CELLS + cell;
+    F[0] += Fs[0];
+    F[1] += Fs[TILE_CELLS];
+    F[2] += Fs[2 * TILE_CELLS];
+  }
+}
+
+// BGK collision with Guo forcing (Eqs. 9-10) of one node's shifted populations f, storing
+// the post-collision populations at node n of fout.
+template <typename real>
+__device__ __forceinline__ void collide_store(const real f[Q], const real F[3],
+                                              real *__restrict__ fout, size_t n,
+                                              const LatParams<real> &P) {
+  // moments: rho = rho0 + sum f~, j = sum c f~ (the rest-state part carries no momentum)
+  real drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    drho += f[i];
+    if (cx(i)) jx += cx(i) > 0 ? f[i] : -f[i];
+    if (cy(i)) jy += cy(i) > 0 ? f[i] : -f[i];
+    if (cz(i)) jz += cz(i) > 0 ? f[i] : -f[i];
+  }
+  // rho = rho0 + drho is never rounded as a whole: 1/rho carries the rounding remainder of
+  // the sum (Fast2Sum, |rho0| >= |drho|), and rho X is expanded as rho0 X + drho X
+  const real rho_hi = P.rho0 + drho;
+  const real rho_lo = (P.rho0 - rho_hi) + drho;
+  const real r1 = real(1) / rho_hi;
+  const real inv_rho = r1 * (real(1) - rho_lo * r1);
+  const real ux = (jx + real(0.5) * F[0]) * inv_rho;
+  const real uy = (jy + real(0.5) * F[1]) * inv_rho;
+  const real uz = (jz + real(0.5) * F[2]) * inv_rho;
+  const real uu15 = real(1.5) * (ux * ux + uy * uy + uz * uz);
+  const real uF3 = real(3) * (ux * F[0] + uy * F[1] + uz * F[2]);
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const real w = (real)wgt(i);
+    const real cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+    const real cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
+    // f^eq - w rho0 = w [drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2)]   (Eq. 10)
+    const real X = real(3) * cu + real(4.5) * cu * cu - uu15;
+    const real feq = w * (drho + P.rho0 * X + drho * X);
+    // Guo source: w (1 - 1/2tau) [3 (c - u).F + 9 (c.F)(c.u)]         (Eq. 9)
+    const real S = w * P.guo * (real(3) * cF - uF3 + real(9) * cF * cu);
+    fout[(size_t)i * P.ncell + n] = f[i] - P.omega * (f[i] - feq) + S;
+  }
+}
+
+// K1: fused stream-collide of every fluid node, one thread per node, with the uniform body
+// force only. The nodes of active interface tiles are collided again by K1t with their
+// interface force, so this pass does not wait for the interface chain of the step.
+template <typename real, bool FIRST>
+__global__ void __launch_bounds__(128) stream_collide_kernel(const real *__restrict__ fin,
+                                                             real *__restrict__ fout,
+                                                             const LatParams<real> P, int z0) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int z = blockIdx.z + z0;
+  if (x >= P.nx) return;
+  const size_t n = ((size_t)z * P.ny + y) * P.nx + x;
+  real f[Q];
+  if (FIRST) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = fin[(size_t)i * P.ncell + n];
+  } else {
+    pull(fin, P, x, y, z, f);
+  }
+  const real F[3] = {P.g[0], P.g[1], P.g[2]};
+  collide_store(f, F, fout, n, P);
+}
+
+// K1t: stream-collide of the fluid nodes of the active tiles with body + interface force,
+// one 64-thread block per tile (grid-stride). Runs after K1 of the same step and overwrites
+// those nodes.
+template <typename real, bool FIRST>
+__global__ void __launch_bounds__(64) stream_collide_tiles_kernel(
+    const real *__restrict__ fin, real *__restrict__ fout, const int *__restrict__ slot_tile,
+    const int *__restrict__ nslots_ptr, const real *__restrict__ Fslot, const LatParams<real> P,
+    int max_slots) {
+  const int nslots = min(*nslots_ptr, max_slots);
+  const int cell = threadIdx.x;
+  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+    const int t = slot_tile[s];
+    const int tx = t % P.ntx, ty = (t / P.ntx) % P.nty, tz = t / (P.ntx * P.nty);
+    const int x = tx * TILE + (cell & 3), y = ty * TILE + ((cell >> 2) & 3),
+              z = tz * TILE + (cell >> 4);
+    if (z >= P.nz || (P.has_walls && (z == 0 || z == P.nz - 1))) continue;
+    const size_t n = ((size_t)z * P.ny + y) * P.nx + x;
+    real f[Q];
+    if (FIRST) {
+#pragma unroll
+      for (int i = 0; i < Q; i++) f[i] = fin[(size_t)i * P.ncell + n];
+    } else {
+      pull(fin, P, x, y, z, f);
+    }
+    const real *Fs = Fslot + (size_t)s * 3 * TILE_CELLS + cell;
+    const real F[3] = {P.g[0] + Fs[0], P.g[1] + Fs[TILE_CELLS], P.g[2] + Fs[2 * TILE_CELLS]};
+    collide_store(f, F, fout, n, P);
+  }
+}
+
+// K1b: velocity after streaming at every node of the active interface tiles.
+// One 64-thread block per active tile (grid-stride over the device-side tile count).
+template <typename real>
+__global__ void __launch_bounds__(64) shell_velocity_kernel(const real *__restrict__ fpost,
+                                                            const int *__restrict__ slot_tile,
+                                                            const int *__restrict__ nslots_ptr,
+                                                            const real *__restrict__ Fslot,
+                                                            real *__restrict__ Uslot,
+                                                            const LatParams<real> P, real ubx,
+                                                            real uby, real ubz, real utx,
+                                                            real uty, real utz, int max_slots) {
+  const int nslots = min(*nslots_ptr, max_slots);
+  const int cell = threadIdx.x;
+  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+    const int t = slot_tile[s];
+    const int tx = t % P.ntx, ty = (t / P.ntx) % P.nty, tz = t / (P.ntx * P.nty);
+    const int x = tx * TILE + (cell & 3), y = ty * TILE + ((cell >> 2) & 3),
+              z = tz * TILE + (cell >> 4);
+    real u[3] = {0, 0, 0};
+    if (z < P.nz) {
+      if (P.has_walls && z == 0) {
+        u[0] = ubx; u[1] = uby; u[2] = ubz;
+      } else if (P.has_walls && z == P.nz - 1) {
+        u[0] = utx; u[1] = uty; u[2] = utz;
+      } else {
+        real f[Q];
+        pull(fpost, P, x, y, z, f);
+        real drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+          drho += f[i];
+          j[0] += cx(i) * f[i];
+          j[1] += cy(i) * f[i];
+          j[2] += cz(i) * f[i];
+        }
+        const real *Fs = Fslot + (size_t)s * 3 * TILE_CELLS + cell;
+        const real rho_hi = P.rho0 + drho;
+        const real rho_lo = (P.rho0 - rho_hi) + drho;
+        const real r1 = real(1) / rho_hi;
+        const real inv_rho = r1 * (real(1) - rho_lo * r1);
+        for (int k = 0; k < 3; k++)
+          u[k] = (j[k] + real(0.5) * (P.g[k] + Fs[k * TILE_CELLS])) * inv_rho;
+      }
+    }
+    real *Us = Uslot + (size_t)s * 3 * TILE_CELLS + cell;
+    Us[0] = u[0];
+    Us[TILE_CELLS] = u[1];
+    Us[2 * TILE_CELLS] = u[2];
+  }
+}
+
+// rho and u of every node of the current post-streaming state (read-back, not on the step).
+template <typename real>
+__global__ void fields_kernel(const real *__restrict__ fstate, int fresh,
+                              const int *__restrict__ tile_slot, const real *__restrict__ Fslot,
+                              const LatParams<real> P, double3 ub, double3 ut, double rho0,
+                              double *__restrict__ rho_out, double *__restrict__ u_out) {
+  const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (n >= P.ncell) return;
+  const int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((size_t)P.nx * P.ny));
+  if (P.has_walls && (z == 0 || z == P.nz - 1)) {
+    const double3 w = z == 0 ? ub : ut;
+    rho_out[n] = rho0;
+    u_out[3 * n] = w.x; u_out[3 * n + 1] = w.y; u_out[3 * n + 2] = w.z;
+    return;
+  }
+  real f[Q];
+  if (fresh) {
+    for (int i = 0; i < Q; i++) f[i] = fstate[(size_t)i * P.ncell + n];
+  } else {
+    pull(fstate, P, x, y, z, f);
+  }
+  double drho = 0, j[3] = {0, 0, 0};
+  for (int i = 0; i < Q; i++) {
+    drho += (double)f[i];
+    j[0] += cx(i) * (double)f[i];
+    j[1] += cy(i) * (double)f[i];
+    j[2] += cz(i) * (double)f[i];
+  }
+  real F[3];
+  tile_force(tile_slot, Fslot, P, x, y, z, F);
+  const double rho = rho0 + drho;
+  rho_out[n] = rho;
+  for (int k = 0; k < 3; k++) u_out[3 * n + k] = (j[k] + 0.5 * (double)F[k]) / rho;
+}
+
+template <typename real>
+__global__ void populations_kernel(const real *__restrict__ fstate, int fresh,
+                                   const LatParams<real> P, double rho0,
+                                   double *__restrict__ f_out) {
+  const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (n >= P.ncell) return;
+  const int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((size_t)P.nx * P.ny));
+  if (P.has_walls && (z == 0 || z == P.nz - 1)) {
+    for (int i = 0; i < Q; i++) f_out[(size_t)i * P.ncell + n] = 0.0;
+    return;
+  }
+  real f[Q];
+  if (fresh) {
+    for (int i = 0; i < Q; i++) f[i] = fstate[(size_t)i * P.ncell + n];
+  } else {
+    pull(fstate, P, x, y, z, f);
+  }
+  for (int i = 0; i < Q; i++) f_out[(size_t)i * P.ncell + n] = wgt(i) * rho0 + (double)f[i];
+}
+
+template <typename real>
+__global__ void init_equilibrium_kernel(real *__restrict__ fstate, const LatParams<real> P,
+                                        double rho0, const double *__restrict__ rho_in,
+                                        const double *__restrict__ u_in) {
+  const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (n >= P.ncell) return;
+  const int z = (int)(n / ((size_t)P.nx * P.ny));
+  const bool wall = P.has_walls && (z == 0 || z == P.nz - 1);
+  const double rho = rho_in[n];
+  const double ux = u_in[3 * n], uy = u_in[3 * n + 1], uz = u_in[3 * n + 2];
+  const double uu = ux * ux + uy * uy + uz * uz;
+  for (int i = 0; i < Q; i++) {
+    const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+    const double v = wgt(i) * ((rho - rho0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+    fstate[(size_t)i * P.ncell + n] = wall ? real(0) : (real)v;
+  }
+}
+
+template <typename real>
+cudaError_t stream_collide_t(Ctx &c, int first, cudaStream_t st) {
+  const LatParams<real> P = lat_params<real>(c);
+  const int z0 = c.has_walls ? 1 : 0;
+  const int nzf = c.has_walls ? c.nz - 2 : c.nz;
+  const int bx = c.nx < 128 ? c.nx : 128;
+  dim3 grid((c.nx + bx - 1) / bx, c.ny, nzf);
+  const real *fin = (const real *)c.f[c.cur];
+  real *fout = (real *)c.f[c.cur ^ 1];
+  if (first)
+    stream_collide_kernel<real, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+  else
+    stream_collide_kernel<real, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t stream_collide_tiles_t(Ctx &c, int first, cudaStream_t st) {
+  const LatParams<real> P = lat_params<real>(c);
+  int grid = c.sm_count * 16;
+  if (grid > c.max_slots) grid = c.max_slots;
+  if (grid < 1) grid = 1;
+  const real *fin = (const real *)c.f[c.cur];
+  real *fout = (real *)c.f[c.cur ^ 1];
+  if (first)
+    stream_collide_tiles_kernel<real, true><<<grid, TILE_CELLS, 0, st>>>(
+        fin, fout, c.slot_tile[c.map], c.counters + c.map, (const real *)c.Fslot[c.map], P,
+        c.max_slots);
+  else
+    stream_collide_tiles_kernel<real, false><<<grid, TILE_CELLS, 0, st>>>(
+        fin, fout, c.slot_tile[c.map], c.counters + c.map, (const real *)c.Fslot[c.map], P,
+        c.max_slots);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t shell_velocity_t(Ctx &c, cudaStream_t st) {
+  const LatParams<real> P = lat_params<real>(c);
+  int grid = c.sm_count * 16;
+  if (grid > c.max_slots) grid = c.max_slots;
+  if (grid < 1) grid = 1;
+  shell_velocity_kernel<real><<<grid, TILE_CELLS, 0, st>>>(
+      (const real *)c.f[c.cur], c.slot_tile[c.map], c.counters + c.map, (const real *)c.Fslot[c.map],
+      (real *)c.Uslot, P, (real)c.ub[0], (real)c.ub[1], (real)c.ub[2], (real)c.ut[0],
+      (real)c.ut[1], (real)c.ut[2], c.max_slots);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_stream_collide(Ctx &c, int first, cudaStream_t s) {
+  return c.precision == IBLB_FP64 ? stream_collide_t<double>(c, first, s)
+                                  : stream_collide_t<float>(c, first, s);
+}
+
+cudaError_t launch_stream_collide_tiles(Ctx &c, int first, cudaStream_t s) {
+  return c.precision == IBLB_FP64 ? stream_collide_tiles_t<double>(c, first, s)
+                                  : stream_collide_tiles_t<float>(c, first, s);
+}
+
+cudaError_t launch_shell_velocity(Ctx &c, cudaStream_t s) {
+  return c.precision == IBLB_FP64 ? shell_velocity_t<double>(c, s) : shell_velocity_t<float>(c, s);
+}
+
+cudaError_t launch_fields(Ctx &c, double *rho_dev, double *u_dev) {
+  const int blocks = (int)((c.ncell + 255) / 256);
+  const double3 ub = make_double3(c.ub[0], c.ub[1], c.ub[2]);
+  const double3 ut = make_double3(c.ut[0], c.ut[1], c.ut[2]);
+  // the force of the last spreading step lives in the map that step used
+  const int *ts = (c.nv && c.have_force) ? c.tile_slot[c.map ^ 1] : nullptr;
+  if (c.precision == IBLB_FP64) {
+    fields_kernel<double><<<blocks, 256, 0, c.stream>>>(
+        (const double *)c.f[c.cur], c.fresh, ts, (const double *)c.Fslot[c.map ^ 1], lat_params<double>(c),
+        ub, ut, c.rho0, rho_dev, u_dev);
+  } else {
+    fields_kernel<float><<<blocks, 256, 0, c.stream>>>(
+        (const float *)c.f[c.cur], c.fresh, ts, (const float *)c.Fslot[c.map ^ 1], lat_params<float>(c), ub,
+        ut, c.rho0, rho_dev, u_dev);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_populations(Ctx &c, double *f_dev) {
+  const int blocks = (int)((c.ncell + 255) / 256);
+  if (c.precision == IBLB_FP64)
+    populations_kernel<double><<<blocks, 256, 0, c.stream>>>(
+        (const double *)c.f[c.cur], c.fresh, lat_params<double>(c), c.rho0, f_dev);
+  else
+    populations_kernel<float><<<blocks, 256, 0, c.stream>>>(
+        (const float *)c.f[c.cur], c.fresh, lat_params<float>(c), c.rho0, f_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_equilibrium(Ctx &c, const double *rho_dev, const double *u_dev) {
+  const int blocks = (int)((c.ncell + 255) / 256);
+  if (c.precision == IBLB_FP64)
+    init_equilibrium_kernel<double><<<blocks, 256, 0, c.stream>>>(
+        (double *)c.f[c.cur], lat_params<double>(c), c.rho0, rho_dev, u_dev);
+  else
+    init_equilibrium_kernel<float><<<blocks, 256, 0, c.stream>>>(
+        (float *)c.f[c.cur], lat_params<float>(c), c.rho0, rho_dev, u_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace iblb

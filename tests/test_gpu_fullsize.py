@@ -1,0 +1,68 @@
+"""Parity at the full size of the benchmark workload (256^3 lattice, 40962-vertex mesh,
+FP32, the launch configuration bench.py times): nodal forces and the spread force field in
+full, one complete coupled step against one oracle step, and mass conservation over many
+steps (a property that holds at any size)."""
+import numpy as np
+import pytest
+
+from pairs import make_pair, rel_l2
+from paper_2305_18919_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def full_pair():
+    wl = inputs.shear_256_fp32()
+    ref, gpu = make_pair(wl, "fp32")
+    q = inputs.perturb(wl.mesh()[0], 0.05, seed=17)  # a slightly deformed interface
+    ref.set_vertices(q)
+    gpu.set_vertices(q)
+    yield wl, ref, gpu
+    ref.close()
+    gpu.close()
+
+
+def test_full_size_forces_and_spread(full_pair):
+    wl, ref, gpu = full_pair
+    phi_ref, _ = ref.forces()
+    assert rel_l2(gpu.forces(), phi_ref) < 2e-6
+    F_ref = ref.force_field()
+    F = gpu.force_field()
+    support = np.abs(F_ref).sum(-1) > 0
+    assert support.sum() > 50000
+    assert rel_l2(F[support], F_ref[support]) < 2e-6
+    assert np.abs(F[~support]).max() == 0.0
+
+
+def test_full_size_one_step(full_pair):
+    wl, ref, gpu = full_pair
+    ref.step(1)
+    gpu.step(1)
+    assert rel_l2(gpu.vertex_velocities(), ref.vertex_velocities()) < 1e-5
+    assert np.abs(gpu.vertices() - ref.vertices()).max() < 1e-9 * wl.radius
+    r0, u0 = ref.fields()
+    r1, u1 = gpu.fields()
+    assert rel_l2(u1, u0) < 1e-5
+    assert rel_l2(r1, r0) < 1e-6
+    # populations at a random sample of nodes, including the wall-adjacent layers
+    f0 = ref.populations()
+    f1 = gpu.populations()
+    rng = np.random.default_rng(3)
+    z = np.concatenate([[1, 254], rng.integers(1, 255, 200)])
+    y = rng.integers(0, 256, z.size)
+    x = rng.integers(0, 256, z.size)
+    np.testing.assert_allclose(f1[:, z, y, x], f0[:, z, y, x], rtol=0, atol=2e-8)
+
+
+def test_full_size_mass_conservation():
+    from paper_2305_18919_gb300 import binding
+    wl = inputs.shear_256_fp32()
+    lat = binding.Lattice.from_workload(wl, precision="fp32")
+    m0 = lat.populations()[:, 1:-1].sum()
+    lat.step(50)
+    m1 = lat.populations()[:, 1:-1].sum()
+    assert abs(m1 - m0) / m0 < 1e-9
+    V, V0 = lat.volume()
+    assert abs(V / V0 - 1) < 1e-3
+    lat.close()
