@@ -151,6 +151,26 @@ int64_t iblb_steps_done(const iblb_ctx *ctx);
 int iblb_set_profiling(iblb_ctx *ctx, int32_t on);
 int iblb_profile(iblb_ctx *ctx, double *k1_ms, int64_t *k1_launches, int64_t *kernel_launches);
 
+/* Enclosed volume of a closed, outward-oriented triangle mesh, for callers that cannot allocate
+   device memory. The paper has no counterpart: this is a library service. It computes
+   V = sum over faces of (x0 - c) . ((x1 - x0) x (x2 - x0)) / 6 in double, the same volume the
+   interface forces use (iblb_read_volume), from caller-owned device arrays: q_dev [nv][3]
+   doubles, faces_dev [nf][3] int32 (indices into q_dev), centre = host pointer to 3 doubles
+   (any fixed point; a point near the mesh limits rounding), V_dev = device pointer to one
+   double that receives V. Work is queued on `cuda_stream` (a cudaStream_t, NULL = legacy
+   default stream); the call does not synchronise.
+   Nothing is allocated: the only scratch is a 32 KB array of per-block partial sums that the
+   library holds on every device that loads it, until the process exits. Callers in a host
+   framework that owns all device memory, or in a loop that must not pay for cudaMalloc's
+   device-wide synchronisation, can use it. The first call on each device looks up that
+   array's device address, so make the first call before any stream capture begins.
+   Limits and errors: nf <= 1,048,576 (IBLB_ECAPACITY beyond), nf >= 1 and non-NULL pointers
+   (IBLB_EINVAL otherwise), IBLB_ECUDA if a launch fails. Every call shares the one array and
+   overwrites the partials it uses, so calls that overlap on the GPU (on different streams)
+   race and must be ordered by the caller. */
+int iblb_mesh_volume_noalloc(const double *q_dev, const int32_t *faces_dev, int32_t nf,
+                             const double *centre, double *V_dev, void *cuda_stream);
+
 /* Bytes moved per fluid cell by one stream-collide launch (19 loads + 19 stores of the
    population type): 152 for IBLB_FP32, 304 for IBLB_FP64. */
 int64_t iblb_bytes_per_cell(const iblb_ctx *ctx);

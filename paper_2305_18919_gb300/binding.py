@@ -78,6 +78,7 @@ SIGNATURES = {
     "iblb_set_profiling": (_i32, [_vp, _i32]),
     "iblb_profile": (_i32, [_vp, _dp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "iblb_bytes_per_cell": (_i64, [_vp]),
+    "iblb_mesh_volume_noalloc": (_i32, [_vp, _vp, _i32, _dp, _vp, _vp]),
 }
 
 
@@ -120,6 +121,17 @@ def _current_stream():
     except Exception:
         pass
     return None
+
+
+def mesh_volume_noalloc(q_dev_ptr: int, faces_dev_ptr: int, nf: int, centre, V_dev_ptr: int,
+                        stream=None) -> int:
+    """iblb_mesh_volume_noalloc on caller-owned device buffers (see include/iblb.h); returns
+    the status code. Nothing is allocated on the device; the call does not synchronise."""
+    c = np.ascontiguousarray(centre, dtype=np.float64).reshape(3)
+    s = stream if stream is not None else _current_stream()
+    return int(lib().iblb_mesh_volume_noalloc(ctypes.c_void_p(q_dev_ptr),
+                                              ctypes.c_void_p(faces_dev_ptr), int(nf), _dptr(c),
+                                              ctypes.c_void_p(V_dev_ptr), s))
 
 
 class Lattice:
