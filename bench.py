@@ -185,7 +185,7 @@ def run_gpu(args, wl, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
-    lat = binding.Lattice.from_workload(wl, precision=wl.precision)
+    lat = binding.Lattice.from_workload(wl, precision=wl.precision, ib_sms=args.ib_sms)
     lat.step(max(3, args.warmup))
     torch.cuda.synchronize()
 
@@ -257,6 +257,7 @@ def run_gpu(args, wl, rank, world):
         except Exception:
             pass
     clocks = clk.summary()
+    ib_sms = lat.interface_sms()
     lat.close()
     if rank != 0:
         if dist:
@@ -267,7 +268,8 @@ def run_gpu(args, wl, rank, world):
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": config_of(wl), "roofline": roofline,
+        "data": "synthetic", "config": dict(config_of(wl), interface_sms=ib_sms),
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "h2d_bytes_per_step": nv * 24,
                 "d2h_bytes_per_step": nv * 24, "steps": e2e_steps,
@@ -287,6 +289,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="shear256")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ib-sms", type=int, default=0,
+                    help="SMs for the interface chain (0: library default, <0: no partition)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

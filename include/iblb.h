@@ -55,7 +55,11 @@ typedef struct {
   int32_t nx, ny, nz;      /* nx, ny multiples of 4; nz >= 3 with walls, >= 4 periodic */
   int32_t precision;       /* IBLB_FP64 or IBLB_FP32 */
   int32_t z_periodic;      /* 0: bounce-back walls at both z ends; 1: periodic z (tests) */
-  int32_t reserved;
+  int32_t ib_sms;          /* SMs given to the interface chain of iblb_step as a partition of
+                              the GPU (green context); the stream-collide passes get the rest.
+                              0: 32 (rounded to the device's partition granularity), < 0: no
+                              partition (both share all SMs, interface stream at top priority).
+                              If the device or driver cannot partition, no partition is used. */
   double tau;              /* BGK relaxation time, > 1/2 (viscosity (tau - 1/2)/3) */
   double rho0;             /* reference density (initial state and moving-wall term) */
   double wall_u_bottom[3]; /* wall velocity at z = 0.5 (tangential components only) */
@@ -170,6 +174,9 @@ int iblb_profile(iblb_ctx *ctx, double *k1_ms, int64_t *k1_launches, int64_t *ke
    race and must be ordered by the caller. */
 int iblb_mesh_volume_noalloc(const double *q_dev, const int32_t *faces_dev, int32_t nf,
                              const double *centre, double *V_dev, void *cuda_stream);
+
+/* SMs of the interface partition of iblb_step (0: no partition, -1: NULL context). */
+int32_t iblb_interface_sms(const iblb_ctx *ctx);
 
 /* Bytes moved per fluid cell by one stream-collide launch (19 loads + 19 stores of the
    population type): 152 for IBLB_FP32, 304 for IBLB_FP64. */

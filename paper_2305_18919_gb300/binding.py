@@ -28,7 +28,7 @@ _PRECISION = {"fp64": IBLB_FP64, "fp32": IBLB_FP32}
 class iblb_lattice_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("z_periodic", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("ib_sms", ctypes.c_int32), ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("wall_u_bottom", ctypes.c_double * 3), ("wall_u_top", ctypes.c_double * 3),
                 ("body_force", ctypes.c_double * 3)]
 
@@ -78,6 +78,7 @@ SIGNATURES = {
     "iblb_set_profiling": (_i32, [_vp, _i32]),
     "iblb_profile": (_i32, [_vp, _dp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "iblb_bytes_per_cell": (_i64, [_vp]),
+    "iblb_interface_sms": (_i32, [_vp]),
     "iblb_mesh_volume_noalloc": (_i32, [_vp, _vp, _i32, _dp, _vp, _vp]),
 }
 
@@ -138,12 +139,14 @@ class Lattice:
     """One IB-LB context (lattice + optional interface mesh) on the current CUDA device."""
 
     def __init__(self, nx, ny, nz, tau, rho0=1.0, wall_u_bottom=(0, 0, 0), wall_u_top=(0, 0, 0),
-                 body_force=(0, 0, 0), precision="fp32", z_periodic=False, stream=None):
+                 body_force=(0, 0, 0), precision="fp32", z_periodic=False, stream=None,
+                 ib_sms=0):
         self._L = lib()
         d = iblb_lattice_desc()
         d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
         d.precision = _PRECISION[precision] if isinstance(precision, str) else int(precision)
         d.z_periodic = int(bool(z_periodic))
+        d.ib_sms = int(ib_sms)
         d.tau, d.rho0 = float(tau), float(rho0)
         d.wall_u_bottom[:] = [float(v) for v in wall_u_bottom]
         d.wall_u_top[:] = [float(v) for v in wall_u_top]
@@ -159,9 +162,9 @@ class Lattice:
             raise IBLBError(rc, "iblb_create failed (invalid description or CUDA unavailable)")
 
     @classmethod
-    def from_workload(cls, wl, precision=None, z_periodic=False, stream=None):
+    def from_workload(cls, wl, precision=None, z_periodic=False, stream=None, ib_sms=0):
         lat = cls(wl.nx, wl.ny, wl.nz, wl.tau, 1.0, wl.wall_u_bottom, wl.wall_u_top,
-                  wl.body_force, precision or wl.precision, z_periodic, stream)
+                  wl.body_force, precision or wl.precision, z_periodic, stream, ib_sms)
         v, f = wl.mesh()
         lat.add_mesh(v, f)
         lat.set_interface(wl.alpha, wl.kV, wl.eps, wl.xi, wl.wall_force_on, wl.volume_force_on)
@@ -284,6 +287,9 @@ class Lattice:
         kl = _i64()
         self._check(self._L.iblb_profile(self.h, ctypes.byref(ms), ctypes.byref(k1), ctypes.byref(kl)))
         return ms.value, k1.value, kl.value
+
+    def interface_sms(self) -> int:
+        return int(self._L.iblb_interface_sms(self.h))
 
     def bytes_per_cell(self) -> int:
         return int(self._L.iblb_bytes_per_cell(self.h))

@@ -8,6 +8,9 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "iblb_internal.cuh"
 
 using iblb::Ctx;
@@ -100,6 +103,154 @@ cudaEvent_t pooled_event(Ctx &c) {
   return c.ev_pool[c.ev_used++];
 }
 
+// Driver entry points for SM partitions (green contexts), looked up at run time so that the
+// library loads without the driver library present.
+struct GreenApi {
+  PFN_cuDeviceGet_v2000 device_get = nullptr;
+  PFN_cuDeviceGetDevResource_v12040 get_resource = nullptr;
+  PFN_cuDevSmResourceSplitByCount_v12040 split = nullptr;
+  PFN_cuDevResourceGenerateDesc_v12040 make_desc = nullptr;
+  PFN_cuGreenCtxCreate_v12040 create = nullptr;
+  PFN_cuGreenCtxDestroy_v12040 destroy = nullptr;
+  PFN_cuGreenCtxStreamCreate_v12050 stream_create = nullptr;
+  PFN_cuStreamDestroy_v4000 stream_destroy = nullptr;
+};
+
+bool green_api(GreenApi &g) {
+  struct Entry {
+    const char *name;
+    void **fn;
+    unsigned version;
+  } entries[] = {{"cuDeviceGet", (void **)&g.device_get, 2000},
+                 {"cuDeviceGetDevResource", (void **)&g.get_resource, 12040},
+                 {"cuDevSmResourceSplitByCount", (void **)&g.split, 12040},
+                 {"cuDevResourceGenerateDesc", (void **)&g.make_desc, 12040},
+                 {"cuGreenCtxCreate", (void **)&g.create, 12040},
+                 {"cuGreenCtxDestroy", (void **)&g.destroy, 12040},
+                 {"cuGreenCtxStreamCreate", (void **)&g.stream_create, 12050},
+                 {"cuStreamDestroy", (void **)&g.stream_destroy, 4000}};
+  for (auto &e : entries) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(e.name, e.fn, e.version, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || *e.fn == nullptr)
+      return false;
+  }
+  return true;
+}
+
+// Split the device's SMs into an interface partition of about `want` SMs and a lattice
+// partition with the rest, each with its own stream. Returns false (and leaves nothing
+// behind) when the device or driver cannot partition.
+bool make_partitions(Ctx &c, int want, int prio_hi) {
+  GreenApi g;
+  if (!green_api(g)) return false;
+  int ord = 0;
+  CUdevice dev;
+  if (cudaGetDevice(&ord) != cudaSuccess || g.device_get(&dev, ord) != CUDA_SUCCESS) return false;
+  CUdevResource all, part, rest;
+  unsigned int groups = 1;
+  if (g.get_resource(dev, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS) return false;
+  if (g.split(&part, &groups, &all, &rest, 0, (unsigned)want) != CUDA_SUCCESS || groups != 1 ||
+      rest.sm.smCount < part.sm.smCount)
+    return false;
+  CUdevResourceDesc d_ib, d_lat;
+  if (g.make_desc(&d_ib, &part, 1) != CUDA_SUCCESS || g.make_desc(&d_lat, &rest, 1) != CUDA_SUCCESS)
+    return false;
+  CUgreenCtx gi = nullptr, gl = nullptr;
+  CUstream si = nullptr, sl = nullptr;
+  bool ok = g.create(&gi, d_ib, dev, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
+            g.create(&gl, d_lat, dev, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
+            g.stream_create(&si, gi, CU_STREAM_NON_BLOCKING, prio_hi) == CUDA_SUCCESS &&
+            g.stream_create(&sl, gl, CU_STREAM_NON_BLOCKING, 0) == CUDA_SUCCESS;
+  if (!ok) {
+    if (si) g.stream_destroy(si);
+    if (sl) g.stream_destroy(sl);
+    if (gi) g.destroy(gi);
+    if (gl) g.destroy(gl);
+    return false;
+  }
+  c.green[0] = gi;
+  c.green[1] = gl;
+  c.ib = (cudaStream_t)si;
+  c.ls = (cudaStream_t)sl;
+  c.ib_sms = (int)part.sm.smCount;
+  return true;
+}
+
+void free_partitions(Ctx &c) {
+  GreenApi g;
+  if (!c.green[0] || !green_api(g)) return;
+  if (c.ib) g.stream_destroy((CUstream)c.ib);
+  if (c.ls) g.stream_destroy((CUstream)c.ls);
+  g.destroy((CUgreenCtx)c.green[0]);
+  g.destroy((CUgreenCtx)c.green[1]);
+  c.ib = c.ls = nullptr;
+  c.green[0] = c.green[1] = nullptr;
+}
+
+// Reference shape of a mesh: centre (mean vertex), per-face inverse metric and area, the
+// reference edges A, B, X0 - centre and the centroid heights above the wall planes zb, zt of
+// each face, and the enclosed volume V0.
+bool reference_shape(const double *verts, int nv, const int32_t *faces, int nf, double zb,
+                     double zt, std::vector<double> &fref, std::vector<double> &fgeo,
+                     double centre[3], double *V0_out) {
+  fref.assign((size_t)4 * nf, 0.0);
+  fgeo.assign((size_t)12 * nf, 0.0);
+  for (int k = 0; k < 3; k++) centre[k] = 0.0;
+  for (int i = 0; i < nv; i++)
+    for (int k = 0; k < 3; k++) centre[k] += verts[3 * i + k] / nv;
+  double V0 = 0.0;
+  for (int j = 0; j < nf; j++) {
+    const double *X0 = verts + 3 * faces[3 * j], *X1 = verts + 3 * faces[3 * j + 1],
+                 *X2 = verts + 3 * faces[3 * j + 2];
+    double a[3], b[3], r0[3], r1[3], r2[3];
+    for (int k = 0; k < 3; k++) {
+      a[k] = X1[k] - X0[k];
+      b[k] = X2[k] - X0[k];
+      r0[k] = X0[k] - centre[k];
+      r1[k] = X1[k] - centre[k];
+      r2[k] = X2[k] - centre[k];
+    }
+    const double g11 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    const double g12 = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    const double g22 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const double det = g11 * g22 - g12 * g12;
+    if (!(det > 0)) return false;
+    fref[4 * j] = g22 / det;
+    fref[4 * j + 1] = -g12 / det;
+    fref[4 * j + 2] = g11 / det;
+    fref[4 * j + 3] = 0.5 * std::sqrt(det);
+    for (int k = 0; k < 3; k++) {
+      fgeo[12 * j + k] = a[k];
+      fgeo[12 * j + 3 + k] = b[k];
+      fgeo[12 * j + 6 + k] = r0[k];
+    }
+    const double gz = (X0[2] + X1[2] + X2[2]) / 3.0;
+    fgeo[12 * j + 9] = gz - zb;
+    fgeo[12 * j + 10] = gz - zt;
+    V0 += (r0[0] * (r1[1] * r2[2] - r1[2] * r2[1]) + r0[1] * (r1[2] * r2[0] - r1[0] * r2[2]) +
+           r0[2] * (r1[0] * r2[1] - r1[1] * r2[0])) / 6.0;
+  }
+  *V0_out = V0;
+  return V0 > 0;
+}
+
+// Upload the reference shape (positions X, per-face data) of the context's mesh.
+int upload_reference(Ctx &c, const double *X, const std::vector<double> &fref,
+                     const std::vector<double> &fgeo) {
+  CUDA_TRY(c, cudaMemcpyAsync(c.fref, fref.data(), fref.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c.xref, X, (size_t)3 * c.nv * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  if (c.precision == IBLB_FP64) {
+    CUDA_TRY(c, cudaMemcpyAsync(c.fgeo, fgeo.data(), fgeo.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c.stream));  // the host buffers are the caller's locals
+  } else {
+    std::vector<float> g32(fgeo.begin(), fgeo.end());
+    CUDA_TRY(c, cudaMemcpyAsync(c.fgeo, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  }
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -138,11 +289,17 @@ int iblb_create(const iblb_lattice_desc *d, void *cuda_stream, iblb_ctx **out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev);
   for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc_bytes(&c.f[b], (size_t)iblb::Q * c.ncell * c.real_size);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.f[0], 0, (size_t)iblb::Q * c.ncell * c.real_size, c.stream);
-  // the interface chain gets the highest stream priority so its small kernels are scheduled
-  // between the blocks of the concurrent full-lattice pass instead of after it
+  // The interface chain runs on its own partition of SMs (default 32) so that the concurrent
+  // full-lattice pass keeps the rest undisturbed; without partitions both share the GPU and
+  // the interface stream gets the highest priority, so that its small kernels are scheduled
+  // between the blocks of the full-lattice pass instead of after it.
   int prio_lo = 0, prio_hi = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c.ib, cudaStreamNonBlocking, prio_hi);
+  const int want = d->ib_sms == 0 ? 32 : d->ib_sms;
+  if (e == cudaSuccess && !(want > 0 && make_partitions(c, want, prio_hi))) {
+    e = cudaStreamCreateWithPriority(&c.ib, cudaStreamNonBlocking, prio_hi);
+    c.ls = c.stream;
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_force, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_coll, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_sync, cudaEventDisableTiming);
@@ -162,6 +319,7 @@ void iblb_destroy(iblb_ctx *h) {
   Ctx &c = h->c;
   cudaStreamSynchronize(c.stream);
   if (c.ib) cudaStreamSynchronize(c.ib);
+  if (c.ls) cudaStreamSynchronize(c.ls);
   for (int b = 0; b < 2; b++) {
     dfree(c.f[b]);
     dfree(c.tile_slot[b]);
@@ -169,15 +327,16 @@ void iblb_destroy(iblb_ctx *h) {
     dfree(c.Fslot[b]);
   }
   dfree(c.counters); dfree(c.slot_count); dfree(c.bucket); dfree(c.overflow); dfree(c.Uslot);
-  dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.vf_start); dfree(c.vf_list);
-  dfree(c.fcontrib); dfree(c.fnorm); dfree(c.vol_partial); dfree(c.phi); dfree(c.stencil);
+  dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.xref); dfree(c.fgeo); dfree(c.disp); dfree(c.vf_start); dfree(c.vf_list);
+  dfree(c.fcontrib); dfree(c.fnorm); dfree(c.vol_partial); dfree(c.phi); dfree(c.gvol); dfree(c.stencil);
   dfree(c.dscratch);
   for (cudaEvent_t ev : c.ev_pool) cudaEventDestroy(ev);
   for (cudaEvent_t ev : c.ev_near) cudaEventDestroy(ev);
   if (c.ev_force) cudaEventDestroy(c.ev_force);
   if (c.ev_coll) cudaEventDestroy(c.ev_coll);
   if (c.ev_sync) cudaEventDestroy(c.ev_sync);
-  if (c.ib) cudaStreamDestroy(c.ib);
+  if (c.green[0]) free_partitions(c);
+  else if (c.ib) cudaStreamDestroy(c.ib);
   delete h;
 }
 
@@ -209,36 +368,10 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
   }
   for (int i = 0; i < 3 * nv; i++)
     if (!std::isfinite(verts[i])) return fail(c, IBLB_EINVAL, "non-finite vertex coordinate");
-  // reference shape: centre, per-face inverse metric and area, volume
-  double centre[3] = {0, 0, 0};
-  for (int i = 0; i < nv; i++)
-    for (int k = 0; k < 3; k++) centre[k] += verts[3 * i + k] / nv;
-  std::vector<double> fref((size_t)4 * nf);
-  double V0 = 0.0;
-  for (int j = 0; j < nf; j++) {
-    const double *X0 = verts + 3 * faces[3 * j], *X1 = verts + 3 * faces[3 * j + 1],
-                 *X2 = verts + 3 * faces[3 * j + 2];
-    double a[3], b[3], r0[3], r1[3], r2[3];
-    for (int k = 0; k < 3; k++) {
-      a[k] = X1[k] - X0[k];
-      b[k] = X2[k] - X0[k];
-      r0[k] = X0[k] - centre[k];
-      r1[k] = X1[k] - centre[k];
-      r2[k] = X2[k] - centre[k];
-    }
-    const double g11 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
-    const double g12 = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
-    const double g22 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-    const double det = g11 * g22 - g12 * g12;
-    if (!(det > 0)) return fail(c, IBLB_EINVAL, "degenerate reference face");
-    fref[4 * j] = g22 / det;
-    fref[4 * j + 1] = -g12 / det;
-    fref[4 * j + 2] = g11 / det;
-    fref[4 * j + 3] = 0.5 * std::sqrt(det);
-    V0 += (r0[0] * (r1[1] * r2[2] - r1[2] * r2[1]) + r0[1] * (r1[2] * r2[0] - r1[0] * r2[2]) +
-           r0[2] * (r1[0] * r2[1] - r1[1] * r2[0])) / 6.0;
-  }
-  if (!(V0 > 0)) return fail(c, IBLB_EINVAL, "mesh is not oriented outward (volume <= 0)");
+  std::vector<double> fref, fgeo;
+  double centre[3], V0;
+  if (!reference_shape(verts, nv, faces, nf, 0.5, c.nz - 1.5, fref, fgeo, centre, &V0))
+    return fail(c, IBLB_EINVAL, "degenerate reference face or mesh not oriented outward");
   // vertex -> (face, corner) lists in face order
   std::vector<int> vf_start(nv + 1, 0), vf_list((size_t)3 * nf);
   for (int j = 0; j < 3 * nf; j++) vf_start[faces[j] + 1]++;
@@ -252,7 +385,7 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
   c.nf = nf;
   c.V0 = V0;
   for (int k = 0; k < 3; k++) c.centre[k] = centre[k];
-  c.vol_blocks = (nf + 255) / 256;
+  c.vol_blocks = (nf + 255) / 256;  // one partial volume change per face block
   const size_t rs = c.real_size;
   long ms = 8L * nv;
   if ((size_t)ms > c.ntiles) ms = (long)c.ntiles;
@@ -268,30 +401,34 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
   CUDA_TRY(c, dalloc(&c.qdot, (size_t)3 * nv));
   CUDA_TRY(c, dalloc(&c.faces, (size_t)3 * nf));
   CUDA_TRY(c, dalloc(&c.fref, (size_t)4 * nf));
+  CUDA_TRY(c, dalloc(&c.xref, (size_t)3 * nv));
+  CUDA_TRY(c, dalloc_bytes(&c.fgeo, (size_t)12 * nf * rs));
+  CUDA_TRY(c, dalloc_bytes(&c.disp, (size_t)4 * nv * rs));
   CUDA_TRY(c, dalloc(&c.vf_start, (size_t)nv + 1));
   CUDA_TRY(c, dalloc(&c.vf_list, (size_t)3 * nf));
   CUDA_TRY(c, dalloc_bytes(&c.fcontrib, (size_t)9 * nf * rs));
   CUDA_TRY(c, dalloc_bytes(&c.fnorm, (size_t)3 * nf * rs));
   CUDA_TRY(c, dalloc(&c.vol_partial, (size_t)c.vol_blocks));
-  CUDA_TRY(c, dalloc_bytes(&c.phi, (size_t)3 * nv * rs));
+  CUDA_TRY(c, dalloc_bytes(&c.phi, (size_t)4 * nv * rs));
+  CUDA_TRY(c, dalloc_bytes(&c.gvol, (size_t)4 * nv * rs));
   CUDA_TRY(c, dalloc_bytes(&c.stencil, (size_t)nv * iblb::stencil_record_bytes(c)));
   for (int b = 0; b < 2; b++) {
     CUDA_TRY(c, dalloc(&c.tile_slot[b], c.ntiles));
     CUDA_TRY(c, dalloc(&c.slot_tile[b], (size_t)c.max_slots));
-    CUDA_TRY(c, dalloc_bytes(&c.Fslot[b], (size_t)c.max_slots * 3 * iblb::TILE_CELLS * rs));
+    CUDA_TRY(c, dalloc_bytes(&c.Fslot[b], (size_t)c.max_slots * 4 * iblb::TILE_CELLS * rs));
     CUDA_TRY(c, cudaMemsetAsync(c.tile_slot[b], 0xff, c.ntiles * sizeof(int), c.stream));
   }
   CUDA_TRY(c, dalloc(&c.slot_count, (size_t)c.max_slots));
   CUDA_TRY(c, dalloc(&c.bucket, (size_t)c.max_slots * iblb::BUCKET_CAP));
   CUDA_TRY(c, dalloc(&c.overflow, (size_t)nv));
-  CUDA_TRY(c, dalloc_bytes(&c.Uslot, (size_t)c.max_slots * 3 * iblb::TILE_CELLS * rs));
+  CUDA_TRY(c, dalloc_bytes(&c.Uslot, (size_t)c.max_slots * 4 * iblb::TILE_CELLS * rs));
   CUDA_TRY(c, cudaMemsetAsync(c.counters, 0, 8 * sizeof(int), c.stream));
   CUDA_TRY(c, cudaMemsetAsync(c.qdot, 0, (size_t)3 * nv * sizeof(double), c.stream));
   CUDA_TRY(c, cudaMemcpyAsync(c.q, verts, (size_t)3 * nv * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   CUDA_TRY(c, cudaMemcpyAsync(c.faces, faces, (size_t)3 * nf * sizeof(int), cudaMemcpyHostToDevice, c.stream));
   CUDA_TRY(c, cudaMemcpyAsync(c.vf_start, vf_start.data(), (size_t)(nv + 1) * sizeof(int), cudaMemcpyHostToDevice, c.stream));
   CUDA_TRY(c, cudaMemcpyAsync(c.vf_list, vf_list.data(), (size_t)3 * nf * sizeof(int), cudaMemcpyHostToDevice, c.stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c.fref, fref.data(), fref.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  if (int rc = upload_reference(c, verts, fref, fgeo)) return rc;
   c.map = 0;
   c.have_force = 0;
   int rc = remark(c, 0);
@@ -347,9 +484,10 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
   if (nsteps < 0) return fail(c, IBLB_EINVAL, "nsteps < 0");
   if (nsteps == 0) return IBLB_OK;
   CUDA_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
-  // the library stream starts after everything queued so far on the caller's stream
+  // the library streams start after everything queued so far on the caller's stream
   CUDA_TRY(c, cudaEventRecord(c.ev_sync, c.stream));
   CUDA_TRY(c, cudaStreamWaitEvent(c.ib, c.ev_sync, 0));
+  if (c.ls != c.stream) CUDA_TRY(c, cudaStreamWaitEvent(c.ls, c.ev_sync, 0));
   for (int s = 0; s < nsteps; s++) {
     if (c.nv) {
       CUDA_TRY(c, iblb::launch_face_forces(c, 1, c.ib));
@@ -363,16 +501,16 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
       e0 = pooled_event(c);
       e1 = pooled_event(c);
       if (!e0 || !e1) return fail(c, IBLB_ECUDA, "cudaEventCreate failed");
-      CUDA_TRY(c, cudaEventRecord(e0, c.stream));
+      CUDA_TRY(c, cudaEventRecord(e0, c.ls));
     }
-    CUDA_TRY(c, iblb::launch_stream_collide(c, c.fresh, c.stream));
-    if (c.profiling) CUDA_TRY(c, cudaEventRecord(e1, c.stream));
+    CUDA_TRY(c, iblb::launch_stream_collide(c, c.fresh, c.ls));
+    if (c.profiling) CUDA_TRY(c, cudaEventRecord(e1, c.ls));
     c.k1_launches += 1;
     c.kernel_launches += 1;
     if (c.nv) {
-      CUDA_TRY(c, cudaStreamWaitEvent(c.stream, c.ev_force, 0));
-      CUDA_TRY(c, iblb::launch_stream_collide_tiles(c, c.fresh, c.stream));
-      CUDA_TRY(c, cudaEventRecord(c.ev_coll, c.stream));
+      CUDA_TRY(c, cudaStreamWaitEvent(c.ls, c.ev_force, 0));
+      CUDA_TRY(c, iblb::launch_stream_collide_tiles(c, c.fresh, c.ls));
+      CUDA_TRY(c, cudaEventRecord(c.ev_coll, c.ls));
       c.kernel_launches += 1;
     }
     c.cur ^= 1;
@@ -387,9 +525,13 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
     }
     c.steps_done++;
   }
-  // the caller's stream continues after the interface chain of the last step
+  // the caller's stream continues after the last step on both library streams
   CUDA_TRY(c, cudaEventRecord(c.ev_sync, c.ib));
   CUDA_TRY(c, cudaStreamWaitEvent(c.stream, c.ev_sync, 0));
+  if (c.ls != c.stream) {
+    CUDA_TRY(c, cudaEventRecord(c.ev_coll, c.ls));
+    CUDA_TRY(c, cudaStreamWaitEvent(c.stream, c.ev_coll, 0));
+  }
   int hw = 0;
   if (int rc = read_health(c, &hw)) return rc;
   if (hw) return health_error(c, hw);
@@ -510,7 +652,7 @@ int iblb_save_state(iblb_ctx *h, const char *path) {
   Ctx &c = h->c;
   StateHeader hd;
   memset(&hd, 0, sizeof(hd));
-  memcpy(hd.magic, "IBLBST01", 8);
+  memcpy(hd.magic, "IBLBST02", 8);
   hd.nx = c.nx; hd.ny = c.ny; hd.nz = c.nz; hd.precision = c.precision; hd.has_walls = c.has_walls;
   hd.nv = c.nv; hd.nf = c.nf; hd.fresh = c.fresh; hd.steps_done = c.steps_done;
   hd.tau = c.tau; hd.rho0 = c.rho0; hd.V0 = c.V0;
@@ -521,13 +663,13 @@ int iblb_save_state(iblb_ctx *h, const char *path) {
   const size_t fbytes = (size_t)iblb::Q * c.ncell * c.real_size;
   std::vector<char> fbuf(fbytes);
   std::vector<double> qbuf((size_t)3 * c.nv), qdbuf((size_t)3 * c.nv);
-  std::vector<char> refbuf((size_t)4 * c.nf * sizeof(double));
+  std::vector<double> refbuf((size_t)3 * c.nv);
   std::vector<int> fcs((size_t)3 * c.nf);
   CUDA_TRY(c, cudaMemcpyAsync(fbuf.data(), c.f[c.cur], fbytes, cudaMemcpyDeviceToHost, c.stream));
   if (c.nv) {
     CUDA_TRY(c, cudaMemcpyAsync(qbuf.data(), c.q, qbuf.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(c, cudaMemcpyAsync(qdbuf.data(), c.qdot, qdbuf.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    CUDA_TRY(c, cudaMemcpyAsync(refbuf.data(), c.fref, refbuf.size(), cudaMemcpyDeviceToHost, c.stream));
+    CUDA_TRY(c, cudaMemcpyAsync(refbuf.data(), c.xref, refbuf.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CUDA_TRY(c, cudaMemcpyAsync(fcs.data(), c.faces, fcs.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   }
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
@@ -537,7 +679,7 @@ int iblb_save_state(iblb_ctx *h, const char *path) {
   if (c.nv) {
     ok = ok && fwrite(qbuf.data(), sizeof(double), qbuf.size(), fp) == qbuf.size();
     ok = ok && fwrite(qdbuf.data(), sizeof(double), qdbuf.size(), fp) == qdbuf.size();
-    ok = ok && fwrite(refbuf.data(), 1, refbuf.size(), fp) == refbuf.size();
+    ok = ok && fwrite(refbuf.data(), sizeof(double), refbuf.size(), fp) == refbuf.size();
     ok = ok && fwrite(fcs.data(), sizeof(int), fcs.size(), fp) == fcs.size();
   }
   ok = (fclose(fp) == 0) && ok;
@@ -551,7 +693,7 @@ int iblb_load_state(iblb_ctx *h, const char *path) {
   FILE *fp = fopen(path, "rb");
   if (!fp) return fail(c, IBLB_EINVAL, std::string("cannot open: ") + path);
   StateHeader hd;
-  bool ok = fread(&hd, sizeof(hd), 1, fp) == 1 && memcmp(hd.magic, "IBLBST01", 8) == 0;
+  bool ok = fread(&hd, sizeof(hd), 1, fp) == 1 && memcmp(hd.magic, "IBLBST02", 8) == 0;
   if (!ok || hd.nx != c.nx || hd.ny != c.ny || hd.nz != c.nz || hd.precision != c.precision ||
       hd.has_walls != c.has_walls || hd.nv != c.nv || hd.nf != c.nf) {
     fclose(fp);
@@ -560,13 +702,13 @@ int iblb_load_state(iblb_ctx *h, const char *path) {
   const size_t fbytes = (size_t)iblb::Q * c.ncell * c.real_size;
   std::vector<char> fbuf(fbytes);
   std::vector<double> qbuf((size_t)3 * c.nv), qdbuf((size_t)3 * c.nv);
-  std::vector<char> refbuf((size_t)4 * c.nf * sizeof(double));
+  std::vector<double> refbuf((size_t)3 * c.nv);
   std::vector<int> fcs((size_t)3 * c.nf);
   ok = fread(fbuf.data(), 1, fbytes, fp) == fbytes;
   if (c.nv) {
     ok = ok && fread(qbuf.data(), sizeof(double), qbuf.size(), fp) == qbuf.size();
     ok = ok && fread(qdbuf.data(), sizeof(double), qdbuf.size(), fp) == qdbuf.size();
-    ok = ok && fread(refbuf.data(), 1, refbuf.size(), fp) == refbuf.size();
+    ok = ok && fread(refbuf.data(), sizeof(double), refbuf.size(), fp) == refbuf.size();
     ok = ok && fread(fcs.data(), sizeof(int), fcs.size(), fp) == fcs.size();
   }
   fclose(fp);
@@ -582,12 +724,17 @@ int iblb_load_state(iblb_ctx *h, const char *path) {
   c.steps_done = hd.steps_done;
   CUDA_TRY(c, cudaMemcpyAsync(c.f[c.cur], fbuf.data(), fbytes, cudaMemcpyHostToDevice, c.stream));
   if (c.nv) {
-    c.V0 = hd.V0;
-    for (int k = 0; k < 3; k++) c.centre[k] = hd.centre[k];
+    std::vector<double> fref, fgeo;
+    double centre[3], V0;
+    if (!reference_shape(refbuf.data(), c.nv, fcs.data(), c.nf, 0.5, c.nz - 1.5, fref, fgeo,
+                         centre, &V0))
+      return fail(c, IBLB_EINVAL, "state file has a degenerate reference shape");
+    if (int rc = upload_reference(c, refbuf.data(), fref, fgeo)) return rc;
+    c.V0 = V0;
+    for (int k = 0; k < 3; k++) c.centre[k] = centre[k];
     c.iface = hd.iface;
     CUDA_TRY(c, cudaMemcpyAsync(c.q, qbuf.data(), qbuf.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
     CUDA_TRY(c, cudaMemcpyAsync(c.qdot, qdbuf.data(), qdbuf.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c.fref, refbuf.data(), refbuf.size(), cudaMemcpyHostToDevice, c.stream));
     c.have_force = 0;
     if (int rc = remark(c, c.map)) return rc;
   }
@@ -623,6 +770,8 @@ int iblb_profile(iblb_ctx *h, double *k1_ms, int64_t *k1_launches, int64_t *kern
   *kernel_launches = c.kernel_launches;
   return IBLB_OK;
 }
+
+int32_t iblb_interface_sms(const iblb_ctx *h) { return h ? h->c.ib_sms : -1; }
 
 int64_t iblb_bytes_per_cell(const iblb_ctx *h) {
   return h ? (int64_t)(2 * iblb::Q * h->c.real_size) : -1;

@@ -14,7 +14,8 @@ namespace {
 
 struct Dims {
   int nx, ny, nz, has_walls, ntx, nty, ntz, max_slots;
-  double zb, zt;  // wall planes
+  double zb, zt;              // wall planes
+  double inx, iny, inz;       // 1/nx, 1/ny, 1/nz
 };
 
 Dims dims_of(const Ctx &c) {
@@ -23,65 +24,86 @@ Dims dims_of(const Ctx &c) {
   d.ntx = c.ntx; d.nty = c.nty; d.ntz = c.ntz; d.max_slots = c.max_slots;
   d.zb = 0.5;
   d.zt = c.nz - 1.5;
+  d.inx = 1.0 / c.nx;
+  d.iny = 1.0 / c.ny;
+  d.inz = 1.0 / c.nz;
   return d;
 }
 
-__device__ __forceinline__ int wrapi(int a, int n) {
-  a %= n;
-  return a < 0 ? a + n : a;
-}
+__device__ __forceinline__ int floor_div4(int a) { return a >> 2; }  // arithmetic shift floors
 
-__device__ __forceinline__ int floor_div4(int a) { return a >= 0 ? a >> 2 : -((3 - a) >> 2); }
+// p reduced to [0, n) for a periodic axis (positions are stored unwrapped); inv_n = 1/n, so
+// no double division is issued (slow on this part). Rounding may leave p at -tiny or n.
+__device__ __forceinline__ double wrap_pos(double p, int n, double inv_n) {
+  return p - n * floor(p * inv_n);
+}
 
 __device__ __forceinline__ float log_(float v) { return logf(v); }
 __device__ __forceinline__ double log_(double v) { return log(v); }
 __device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
 __device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
 
-// Lennard-Jones force along z on a centroid at height gz above the wall plane zw (Eq. 19;
+// Lennard-Jones force along z on a centroid at signed height dz above a wall plane (Eq. 19;
 // d points from the wall foot point to the centroid).
 template <typename real>
-__device__ __forceinline__ real lj_fz(double gz, double zw, real eps48, real xi) {
-  const real dz = (real)(gz - zw);
+__device__ __forceinline__ real lj_fz(real dz, real eps48, real xi) {
   const real inv_d2 = real(1) / (dz * dz);
   const real s2 = xi * xi * inv_d2;
   const real s6 = s2 * s2 * s2;
   return eps48 * (s6 * s6 - real(0.5) * s6) * dz * inv_d2;
 }
 
+// Per-face reference data in the population type: A, B (edges), X0 - c, and the reference
+// centroid height above the bottom and the top wall plane; padded to 12.
+constexpr int FGEO = 12;
+
 struct FaceParams {
   double a1, a2, a3;  // alpha
   double eps48, xi;
   int wall_on;
-  double cx, cy, cz;  // fixed point of the volume decomposition
 };
 
-// K3a: one thread per face. Writes the strain + wall force of each corner, the face's
-// volume gradient (a x b)/6, and one partial volume per block (summed in double, warp
-// shuffles in a fixed order).
+// K3a: one thread per face, in the population type. Writes the strain + wall force of each
+// corner, the face's contribution (a x b)/6 to the volume gradient of each of its corners,
+// and one partial sum per block of V_j - V0_j, the change of the face's share of the volume.
 // With reset != 0 it also clears the tile map that the previous step used.
+//
+// V_j = (x0 - c) . (a x b) / 6 for a fixed point c. Written with the displacements
+// u_k = x_k - X_k from the reference shape (da = u1 - u0, db = u2 - u0, reference edges A, B)
+// the change is
+//   6 (V_j - V0_j) = u0 . (a x b) + (X0 - c) . (da x b + A x db),
+// a sum of terms proportional to the displacement, so float arithmetic loses nothing to the
+// cancellation between V and V0 (the per-block partials are summed in double).
 template <typename real>
 __global__ void __launch_bounds__(256) face_kernel(
-    int nf, const int *__restrict__ faces, const double *__restrict__ q,
-    const double *__restrict__ fref, real *__restrict__ fcontrib, real *__restrict__ fnorm,
+    int nf, const int *__restrict__ faces, const Vec4<real> *__restrict__ disp,
+    const double *__restrict__ fref, const real *__restrict__ fgeo,
+    real *__restrict__ fcontrib, real *__restrict__ fnorm,
     double *__restrict__ vol_partial, FaceParams fp, Dims D, int *__restrict__ other_tile_slot,
     const int *__restrict__ other_slot_tile, const int *__restrict__ other_nslots, int reset,
     int *__restrict__ ovf_count) {
   __shared__ double warp_sum[8];
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  double vj = 0.0;
+  real dvj = 0;
   if (j < nf) {
-    const int i0 = faces[3 * j], i1 = faces[3 * j + 1], i2 = faces[3 * j + 2];
-    const double x0[3] = {q[3 * i0], q[3 * i0 + 1], q[3 * i0 + 2]};
-    const double x1[3] = {q[3 * i1], q[3 * i1 + 1], q[3 * i1 + 2]};
-    const double x2[3] = {q[3 * i2], q[3 * i2 + 1], q[3 * i2 + 2]};
-    double ad[3], bd[3];
-    real a[3], b[3];
+    const int iv[3] = {faces[3 * j], faces[3 * j + 1], faces[3 * j + 2]};
+    real u[3][3];
+    for (int c = 0; c < 3; c++) {
+      const Vec4<real> d = disp[iv[c]];
+      u[c][0] = d.x;
+      u[c][1] = d.y;
+      u[c][2] = d.z;
+    }
+    const real *geo = fgeo + FGEO * (size_t)j;  // A, B, X0 - c, centroid heights above walls
+    real A[3], B[3], X0c[3], da[3], db[3], a[3], b[3];
     for (int k = 0; k < 3; k++) {
-      ad[k] = x1[k] - x0[k];
-      bd[k] = x2[k] - x0[k];
-      a[k] = (real)ad[k];
-      b[k] = (real)bd[k];
+      A[k] = geo[k];
+      B[k] = geo[3 + k];
+      X0c[k] = geo[6 + k];
+      da[k] = u[1][k] - u[0][k];
+      db[k] = u[2][k] - u[0][k];
+      a[k] = A[k] + da[k];
+      b[k] = B[k] + db[k];
     }
     const real H11 = (real)fref[4 * j], H12 = (real)fref[4 * j + 1], H22 = (real)fref[4 * j + 2],
                A0 = (real)fref[4 * j + 3];
@@ -105,9 +127,11 @@ __global__ void __launch_bounds__(256) face_kernel(
       f0[k] = ga + gb;
     }
     if (fp.wall_on && D.has_walls) {
-      const double gz = (x0[2] + x1[2] + x2[2]) * (1.0 / 3.0);
-      const real third = (lj_fz<real>(gz, D.zb, (real)fp.eps48, (real)fp.xi) +
-                          lj_fz<real>(gz, D.zt, (real)fp.eps48, (real)fp.xi)) *
+      // centroid height above each wall plane: reference height (from the set-up, in double)
+      // plus the mean displacement
+      const real uz = (u[0][2] + u[1][2] + u[2][2]) * real(1.0 / 3.0);
+      const real third = (lj_fz<real>(geo[9] + uz, (real)fp.eps48, (real)fp.xi) +
+                          lj_fz<real>(geo[10] + uz, (real)fp.eps48, (real)fp.xi)) *
                          real(1.0 / 3.0);
       f0[2] += third;
       f1[2] += third;
@@ -119,23 +143,26 @@ __global__ void __launch_bounds__(256) face_kernel(
       fc[3 + k] = f1[k];
       fc[6 + k] = f2[k];
     }
-    // Volume share of the face, V_j = (x0 - c).(x1 - c) x (x2 - c) / 6 = (x0 - c).(a x b) / 6,
-    // and its gradient. For a closed surface the gradient of V at vertex i does not depend
-    // on the point c, so taking c = x_i for the faces around i gives dV/dq_i = sum (a x b)/6:
-    // the same edge cross product for all three corners, free of the R^2 cancellation of
-    // products of position vectors.
-    const double n0 = ad[1] * bd[2] - ad[2] * bd[1];
-    const double n1 = ad[2] * bd[0] - ad[0] * bd[2];
-    const double n2 = ad[0] * bd[1] - ad[1] * bd[0];
-    vj = ((x0[0] - fp.cx) * n0 + (x0[1] - fp.cy) * n1 + (x0[2] - fp.cz) * n2) * (1.0 / 6.0);
+    // For a closed surface the gradient of V at vertex i does not depend on the point about
+    // which the tetrahedra are taken; with that point at x_i every face around i contributes
+    // (a x b)/6, the same edge cross product for all three corners.
+    const real n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2],
+                       a[0] * b[1] - a[1] * b[0]};
+    const real m[3] = {da[1] * b[2] - da[2] * b[1] + A[1] * db[2] - A[2] * db[1],
+                       da[2] * b[0] - da[0] * b[2] + A[2] * db[0] - A[0] * db[2],
+                       da[0] * b[1] - da[1] * b[0] + A[0] * db[1] - A[1] * db[0]};
+    const real sixth = real(1.0 / 6.0);
     real *fn = fnorm + 3 * (size_t)j;
-    fn[0] = (real)(n0 * (1.0 / 6.0));
-    fn[1] = (real)(n1 * (1.0 / 6.0));
-    fn[2] = (real)(n2 * (1.0 / 6.0));
+    fn[0] = n[0] * sixth;
+    fn[1] = n[1] * sixth;
+    fn[2] = n[2] * sixth;
+    dvj = (u[0][0] * n[0] + u[0][1] * n[1] + u[0][2] * n[2] + X0c[0] * m[0] + X0c[1] * m[1] +
+           X0c[2] * m[2]) * sixth;
   }
-  // block sum of the face volumes, fixed shuffle tree
-  for (int o = 16; o > 0; o >>= 1) vj += __shfl_down_sync(0xffffffffu, vj, o);
-  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = vj;
+  // block sum of V_j - V0_j, fixed shuffle tree (within a warp in the population type)
+  real dw = (real)dvj;
+  for (int o = 16; o > 0; o >>= 1) dw += __shfl_down_sync(0xffffffffu, dw, o);
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = (double)dw;
   __syncthreads();
   if (threadIdx.x < 32) {
     double v = threadIdx.x < (blockDim.x >> 5) ? warp_sum[threadIdx.x] : 0.0;
@@ -150,12 +177,16 @@ __global__ void __launch_bounds__(256) face_kernel(
   }
 }
 
-// Sum of the per-block partial volumes in a fixed order by one warp.
-__device__ __forceinline__ double total_volume(const double *__restrict__ part, int n) {
-  double v = 0.0;
-  for (int k = threadIdx.x; k < n; k += 32) v += part[k];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return __shfl_sync(0xffffffffu, v, 0);
+// kV (V - V0)/V0 from the per-block partial sums of V - V0, by one warp in a fixed order;
+// also returns V.
+__device__ __forceinline__ double volume_coef(const double *__restrict__ part, int n, double V0,
+                                              double kV, int volume_on, double *V_out) {
+  double dv = 0.0;
+  for (int k = threadIdx.x & 31; k < n; k += 32) dv += part[k];
+  for (int o = 16; o > 0; o >>= 1) dv += __shfl_down_sync(0xffffffffu, dv, o);
+  dv = __shfl_sync(0xffffffffu, dv, 0);
+  if (V_out) *V_out = V0 + dv;
+  return volume_on ? kV * dv / V0 : 0.0;
 }
 
 // One-dimensional Peskin weights of the four nodes floor(p)-1 .. floor(p)+2 (Eq. 15).
@@ -173,53 +204,57 @@ __device__ __forceinline__ void peskin_weights(double p, int &base, real w[4]) {
   w[3] = (real(1) + real(2) * r - s) * real(0.125);
 }
 
-struct VertexParams {
-  double V0, kV;
-  int volume_on, vol_blocks;
-};
+// Faces around a vertex gathered with all loads in flight (icosphere valences are 5 and 6).
+constexpr int GATHER_UNROLL = 8;
 
-// K3b: one thread per vertex. Nodal force (Eq. 16) = gathered corner forces minus
-// kV (V - V0)/V0 dV/dq (dV/dq = sum of the face gradients around the vertex), in face order; then the delta stencil of the vertex and its
-// binning into the source tile (the tile that holds its base node).
+// K3b: one thread per vertex. Gathers, in face order, the strain + wall force of the vertex's
+// corners (phi, Eq. 16 without the volume term) and its volume gradient g = dV/dq_i; the
+// volume term -kV (V - V0)/V0 g is added where the force is used (spreading, read-back),
+// after V is complete. Then the delta stencil of the vertex and its binning into the source
+// tile (the tile that holds its base node).
 template <typename real>
 __global__ void __launch_bounds__(256) vertex_kernel(
-    int nv, const double *__restrict__ vol_partial, VertexParams vp,
-    const int *__restrict__ vf_start, const int *__restrict__ vf_list,
+    int nv, const int *__restrict__ vf_start, const int *__restrict__ vf_list,
     const real *__restrict__ fcontrib, const real *__restrict__ fnorm,
-    const double *__restrict__ q, real *__restrict__ phi, StencilRec<real> *__restrict__ stencil,
-    int bin, const int *__restrict__ tile_slot, int *__restrict__ slot_count,
-    int *__restrict__ bucket, int *__restrict__ overflow, int *__restrict__ ovf_count,
-    int *__restrict__ health, int *__restrict__ zero_counter, Dims D) {
-  __shared__ double s_coef;
-  if (threadIdx.x < 32) {
-    const double V = total_volume(vol_partial, vp.vol_blocks);
-    if (threadIdx.x == 0) {
-      const double rel = (V - vp.V0) / vp.V0;
-      s_coef = vp.volume_on ? vp.kV * rel : 0.0;
-      if (blockIdx.x == 0) {
-        if (!(fabs(rel) <= 0.05)) atomicOr(health, H_VOLUME);
-        if (zero_counter) *zero_counter = 0;
+    const double *__restrict__ q, Vec4<real> *__restrict__ phi, Vec4<real> *__restrict__ gvol,
+    StencilRec<real> *__restrict__ stencil, int bin, const int *__restrict__ tile_slot,
+    int *__restrict__ slot_count, int *__restrict__ bucket, int *__restrict__ overflow,
+    int *__restrict__ ovf_count, int *__restrict__ health, int *__restrict__ zero_counter, Dims D) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && zero_counter) *zero_counter = 0;
+  if (i >= nv) return;
+  const int e0 = vf_start[i], e1 = vf_start[i + 1];
+  real F[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+  for (int eb = e0; eb < e1; eb += GATHER_UNROLL) {
+    int fcs[GATHER_UNROLL];
+#pragma unroll
+    for (int u = 0; u < GATHER_UNROLL; u++) fcs[u] = eb + u < e1 ? vf_list[eb + u] : -1;
+#pragma unroll
+    for (int u = 0; u < GATHER_UNROLL; u++) {
+      if (fcs[u] < 0) continue;
+      const int fc = fcs[u];  // face * 3 + corner
+      const int f = fc / 3;
+      for (int k = 0; k < 3; k++) {
+        F[k] += fcontrib[3 * (size_t)fc + k];
+        g[k] += fnorm[3 * (size_t)f + k];
       }
     }
   }
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nv) return;
-  const real coef = (real)s_coef;
-  real F[3] = {0, 0, 0};
-  const int e0 = vf_start[i], e1 = vf_start[i + 1];
-  for (int e = e0; e < e1; e++) {
-    const int fc = vf_list[e];  // face * 3 + corner
-    const int f = fc / 3;
-    for (int k = 0; k < 3; k++) F[k] += fcontrib[3 * (size_t)fc + k] - coef * fnorm[3 * (size_t)f + k];
-  }
-  for (int k = 0; k < 3; k++) phi[3 * (size_t)i + k] = F[k];
+  Vec4<real> pv, gv;
+  pv.x = F[0]; pv.y = F[1]; pv.z = F[2]; pv.w = real(0);
+  gv.x = g[0]; gv.y = g[1]; gv.z = g[2]; gv.w = real(0);
+  phi[i] = pv;
+  gvol[i] = gv;
   if (!bin) return;
   StencilRec<real> rec;
-  for (int k = 0; k < 3; k++) peskin_weights<real>(q[3 * (size_t)i + k], rec.base[k], rec.w[k]);
-  rec.base[0] = wrapi(rec.base[0], D.nx);
-  rec.base[1] = wrapi(rec.base[1], D.ny);
-  if (!D.has_walls) rec.base[2] = wrapi(rec.base[2], D.nz);
+  peskin_weights<real>(wrap_pos(q[3 * (size_t)i], D.nx, D.inx), rec.base[0], rec.w[0]);
+  peskin_weights<real>(wrap_pos(q[3 * (size_t)i + 1], D.ny, D.iny), rec.base[1], rec.w[1]);
+  const double pz = q[3 * (size_t)i + 2];
+  peskin_weights<real>(D.has_walls ? pz : wrap_pos(pz, D.nz, D.inz), rec.base[2], rec.w[2]);
+  // base in [-2, n - 1] on the periodic axes (rounding of the wrap): bring it into [0, n)
+  if (rec.base[0] < 0) rec.base[0] += D.nx;
+  if (rec.base[1] < 0) rec.base[1] += D.ny;
+  if (!D.has_walls && rec.base[2] < 0) rec.base[2] += D.nz;
   rec.pad = 0;
   stencil[i] = rec;
   const int bz = min(max(rec.base[2], 0), D.nz - 1);
@@ -264,34 +299,63 @@ __global__ void __launch_bounds__(256) sort_buckets_kernel(const int *__restrict
   }
 }
 
-// Candidates staged per tile and pass of the spreading kernel.
-constexpr int SPREAD_CHUNK = 64;
+// Candidates staged per tile and pass of the spreading kernel (shared memory: 4 tiles x chunk
+// x 16 values: 16 KB in float, 32 KB in double).
+template <typename real>
+struct SpreadChunk {
+  static constexpr int value = 64;
+};
+
+// w[d] for a run-time d in 0..3 without indexing a local array.
+template <typename real>
+__device__ __forceinline__ real pick4(const real w[4], int d) {
+  return d == 0 ? w[0] : d == 1 ? w[1] : d == 2 ? w[2] : w[3];
+}
 // Active tiles per 64-thread spreading block (16 threads per tile).
 constexpr int SPREAD_TILES = 4;
+
+struct VolumeParams {
+  double V0, kV;
+  int volume_on, vol_blocks;
+};
 
 // K4b: spreading (Eq. 13). A 64-thread block handles 4 active tiles; 16 threads per tile,
 // thread (ly, lz) owns the x-row of 4 nodes (0..3, ly, lz). The candidates of a tile are the
 // vertices binned in its eight source tiles T - {0,1}^3 (every vertex whose stencil reaches
 // T lies there), in bucket order, then the overflow list. When a candidate is staged its
-// one-dimensional weights are re-indexed to the tile's node coordinates, zero where the
-// stencil misses the tile, so the inner loop is a branch-free separable product. Each
-// thread writes its own nodes once: no atomics, and the summation order is fixed by the
-// sorted buckets (the overflow list, normally empty, follows arrival order).
+// nodal force is completed with the volume term and its one-dimensional weights are
+// re-indexed to the tile's node coordinates, zero where the stencil misses the tile, so the
+// inner loop is a branch-free separable product. Each thread writes its own nodes once: no
+// atomics, and the summation order is fixed by the sorted buckets (the overflow list,
+// normally empty, follows arrival order).
 template <typename real>
 __global__ void __launch_bounds__(64) spread_kernel(
     const int *__restrict__ tile_slot, const int *__restrict__ slot_tile,
     const int *__restrict__ nslots_ptr, const int *__restrict__ slot_count,
     const int *__restrict__ bucket, const int *__restrict__ overflow,
     const int *__restrict__ ovf_count_ptr, const StencilRec<real> *__restrict__ stencil,
-    const real *__restrict__ phi, real *__restrict__ Fslot, Dims D) {
+    const Vec4<real> *__restrict__ phi, const Vec4<real> *__restrict__ gvol,
+    const double *__restrict__ vol_partial, VolumeParams vp, int *__restrict__ health,
+    Vec4<real> *__restrict__ Fslot, Dims D) {
+  constexpr int SPREAD_CHUNK = SpreadChunk<real>::value;
   __shared__ int s_src_slot[SPREAD_TILES][8];
   __shared__ int s_src_start[SPREAD_TILES][9];
-  __shared__ real s_wx[SPREAD_TILES][SPREAD_CHUNK][4];
+  __shared__ Vec4<real> s_wx[SPREAD_TILES][SPREAD_CHUNK];
   __shared__ real s_wy[SPREAD_TILES][SPREAD_CHUNK][4];
   __shared__ real s_wz[SPREAD_TILES][SPREAD_CHUNK][4];
-  __shared__ real s_phi[SPREAD_TILES][SPREAD_CHUNK][4];
+  __shared__ Vec4<real> s_phi[SPREAD_TILES][SPREAD_CHUNK];
+  __shared__ double s_coef;
+  __shared__ int s_passes[2];
   const int nslots = min(*nslots_ptr, D.max_slots);
   const int novf = *ovf_count_ptr;
+  if (threadIdx.x < 32) {
+    double V;
+    const double coef = volume_coef(vol_partial, vp.vol_blocks, vp.V0, vp.kV, vp.volume_on, &V);
+    if (threadIdx.x == 0) {
+      s_coef = coef;
+      if (blockIdx.x == 0 && !(fabs(V / vp.V0 - 1.0) <= 0.05)) atomicOr(health, H_VOLUME);
+    }
+  }
   const int tq = threadIdx.x >> 4;  // tile of this thread within the block
   const int r = threadIdx.x & 15;
   const int ly = r & 3, lz = r >> 2;
@@ -335,12 +399,12 @@ __global__ void __launch_bounds__(64) spread_kernel(
       for (int k = 1; k <= 8; k++) s_src_start[tq][k] += s_src_start[tq][k - 1];
     }
     __syncthreads();
+    const real coef = (real)s_coef;
     const int nb = s_src_start[tq][8];
     const int total = active ? nb + novf : 0;
     // the block runs as many passes as its largest tile needs
     int passes = (total + SPREAD_CHUNK - 1) / SPREAD_CHUNK;
-    for (int o = 16; o < 64; o <<= 1) passes = max(passes, __shfl_xor_sync(0xffffffffu, passes, o));
-    __shared__ int s_passes[2];
+    passes = max(passes, __shfl_xor_sync(0xffffffffu, passes, 16));
     if ((threadIdx.x & 31) == 0) s_passes[threadIdx.x >> 5] = passes;
     __syncthreads();
     passes = max(s_passes[0], s_passes[1]);
@@ -351,52 +415,85 @@ __global__ void __launch_bounds__(64) spread_kernel(
       const int c0 = p * SPREAD_CHUNK;
       const int nload = max(0, min(SPREAD_CHUNK, total - c0));
       if (p > 0) __syncthreads();
-      for (int k = r; k < nload; k += 16) {
-        const int g = c0 + k;
-        int v;
-        if (g < nb) {
-          int src = 0;
-          while (g >= s_src_start[tq][src + 1]) src++;
-          v = bucket[(size_t)s_src_slot[tq][src] * BUCKET_CAP + (g - s_src_start[tq][src])];
-        } else {
-          v = overflow[g - nb];
+      // Stage the candidates whose stencil overlaps the tile, keeping their order: lanes of a
+      // tile take 16 candidates per round and a ballot compacts the ones that overlap.
+      const int lane = threadIdx.x & 31;
+      const int wmax = max(nload, __shfl_xor_sync(0xffffffffu, nload, 16));
+      int nkeep = 0;
+      for (int k0 = 0; k0 < wmax; k0 += 16) {
+        const int k = k0 + r;
+        bool keep = false;
+        real wx[4], wy[4], wz[4];
+        Vec4<real> ph;
+        if (k < nload) {
+          const int g = c0 + k;
+          int v;
+          if (g < nb) {
+            int src = 0;
+            while (g >= s_src_start[tq][src + 1]) src++;
+            v = bucket[(size_t)s_src_slot[tq][src] * BUCKET_CAP + (g - s_src_start[tq][src])];
+          } else {
+            v = overflow[g - nb];
+          }
+          const StencilRec<real> rec = stencil[v];
+          real sx = 0, sy = 0, sz = 0;
+          for (int l = 0; l < 4; l++) {
+            int dx = X0 + l - rec.base[0];
+            dx = dx < 0 ? dx + D.nx : dx;
+            int dy = Y0 + l - rec.base[1];
+            dy = dy < 0 ? dy + D.ny : dy;
+            int dz = Z0 + l - rec.base[2];
+            if (!D.has_walls) dz = dz < 0 ? dz + D.nz : dz;
+            wx[l] = dx < 4 ? pick4(rec.w[0], dx) : real(0);
+            wy[l] = dy < 4 ? pick4(rec.w[1], dy) : real(0);
+            wz[l] = (unsigned)dz < 4u ? pick4(rec.w[2], dz) : real(0);
+            sx += wx[l];
+            sy += wy[l];
+            sz += wz[l];
+          }
+          keep = sx > real(0) && sy > real(0) && sz > real(0);
+          if (keep) {
+            const Vec4<real> pv = phi[v], gv = gvol[v];
+            ph = Vec4<real>{pv.x - coef * gv.x, pv.y - coef * gv.y, pv.z - coef * gv.z, real(0)};
+          }
         }
-        const StencilRec<real> &rec = stencil[v];
-        for (int l = 0; l < 4; l++) {
-          int dx = X0 + l - rec.base[0];
-          dx = dx < 0 ? dx + D.nx : dx;
-          int dy = Y0 + l - rec.base[1];
-          dy = dy < 0 ? dy + D.ny : dy;
-          int dz = Z0 + l - rec.base[2];
-          if (!D.has_walls) dz = dz < 0 ? dz + D.nz : dz;
-          s_wx[tq][k][l] = dx < 4 ? rec.w[0][dx] : real(0);
-          s_wy[tq][k][l] = dy < 4 ? rec.w[1][dy] : real(0);
-          s_wz[tq][k][l] = (unsigned)dz < 4u ? rec.w[2][dz] : real(0);
+        const unsigned mine = (__ballot_sync(0xffffffffu, keep) >> (lane & 16)) & 0xffffu;
+        if (keep) {
+          const int pos = nkeep + __popc(mine & ((1u << r) - 1u));
+          s_wx[tq][pos] = Vec4<real>{wx[0], wx[1], wx[2], wx[3]};
+          for (int l = 0; l < 4; l++) {
+            s_wy[tq][pos][l] = wy[l];
+            s_wz[tq][pos][l] = wz[l];
+          }
+          s_phi[tq][pos] = ph;
         }
-        s_phi[tq][k][0] = phi[3 * (size_t)v];
-        s_phi[tq][k][1] = phi[3 * (size_t)v + 1];
-        s_phi[tq][k][2] = phi[3 * (size_t)v + 2];
+        nkeep += __popc(mine);
       }
       __syncthreads();
-      for (int k = 0; k < nload; k++) {
+      for (int k = 0; k < nkeep; k++) {
         const real t = s_wy[tq][k][ly] * s_wz[tq][k][lz];
-        if (t == real(0)) continue;
-        const real g0 = t * s_phi[tq][k][0], g1 = t * s_phi[tq][k][1], g2 = t * s_phi[tq][k][2];
-        for (int l = 0; l < 4; l++) {
-          const real wx = s_wx[tq][k][l];
-          acc[l][0] += wx * g0;
-          acc[l][1] += wx * g1;
-          acc[l][2] += wx * g2;
-        }
+        const Vec4<real> ph = s_phi[tq][k];
+        const Vec4<real> wxv = s_wx[tq][k];
+        const real g0 = t * ph.x, g1 = t * ph.y, g2 = t * ph.z;
+        acc[0][0] += wxv.x * g0; acc[0][1] += wxv.x * g1; acc[0][2] += wxv.x * g2;
+        acc[1][0] += wxv.y * g0; acc[1][1] += wxv.y * g1; acc[1][2] += wxv.y * g2;
+        acc[2][0] += wxv.z * g0; acc[2][1] += wxv.z * g1; acc[2][2] += wxv.z * g2;
+        acc[3][0] += wxv.w * g0; acc[3][1] += wxv.w * g1; acc[3][2] += wxv.w * g2;
       }
     }
     if (active) {
       // force landing on a wall layer is dropped
       const int Z = Z0 + lz;
       const bool drop = D.has_walls && (Z == 0 || Z >= D.nz - 1);
-      real *Fs = Fslot + (size_t)b * 3 * TILE_CELLS + 4 * ly + 16 * lz;
-      for (int l = 0; l < 4; l++)
-        for (int k = 0; k < 3; k++) Fs[k * TILE_CELLS + l] = drop ? real(0) : acc[l][k];
+      Vec4<real> *Fs = Fslot + (size_t)b * TILE_CELLS + 4 * ly + 16 * lz;
+      for (int l = 0; l < 4; l++) {
+        Vec4<real> o;
+        o.x = drop ? real(0) : acc[l][0];
+        o.y = drop ? real(0) : acc[l][1];
+        o.z = drop ? real(0) : acc[l][2];
+        o.w = real(0);
+        Fs[l] = o;
+      }
     }
   }
 }
@@ -418,29 +515,45 @@ __device__ __forceinline__ void claim_tile(int t, int *tile_slot, int *slot_tile
   }
 }
 
-// Mark tile e (0..7: one bit per axis picks the lower or upper tile) covered by the stencil
-// of position p.
-__device__ __forceinline__ void mark_tiles(const double p[3], int e, const Dims &D,
-                                           int *tile_slot, int *slot_tile, int *nslots,
-                                           int *slot_count, int *health) {
+// Tiles covered along one axis by the stencil of coordinate p: t0 (lower) and t1 (upper,
+// equal to t0 when the four nodes fall in one tile); `ok1` tells whether t1 is a distinct
+// tile that exists. Periodic axes wrap; along a walled z axis tiles beyond the lattice are
+// skipped (valid flags).
+struct AxisTiles {
+  int t0, t1;
+  bool ok0, ok1;
+};
+
+__device__ __forceinline__ AxisTiles axis_tiles(double p, int nt, double inv_n, bool periodic) {
+  AxisTiles a;
+  if (periodic) p = wrap_pos(p, 4 * nt, inv_n);
+  const int b = (int)floor(p) - 1;
+  int t0 = floor_div4(b), t1 = floor_div4(b + 3);
+  a.ok1 = t1 != t0;
+  if (periodic) {  // b in [-2, 4 nt - 1]: t0 in [-1, nt - 1], t1 in [0, nt]
+    t0 = t0 < 0 ? t0 + nt : t0;
+    t1 = t1 >= nt ? t1 - nt : t1;
+    a.ok0 = true;
+    a.ok1 = a.ok1 && t1 != t0;  // a short periodic axis may wrap onto the same tile
+  } else {
+    a.ok0 = t0 >= 0 && t0 < nt;
+    a.ok1 = a.ok1 && t1 >= 0 && t1 < nt;
+  }
+  a.t0 = t0;
+  a.t1 = t1;
+  return a;
+}
+
+// Claim, in map (tile_slot, slot_tile, nslots), tile e (bit k picks the upper tile along
+// axis k) of the stencil described by ax.
+__device__ __forceinline__ void mark_tile(const AxisTiles ax[3], int e, const Dims &D,
+                                          int *tile_slot, int *slot_tile, int *nslots,
+                                          int *slot_count, int *health) {
   int t[3];
-  const int n[3] = {D.nx, D.ny, D.nz};
-  const int nt[3] = {D.ntx, D.nty, D.ntz};
   for (int k = 0; k < 3; k++) {
-    const int b = (int)floor(p[k]) - 1;
-    const int t0 = floor_div4(b), t1 = floor_div4(b + 3);
-    const int pick = (e >> k) & 1;
-    if (pick && t1 == t0) return;  // the stencil stays in one tile along this axis
-    int tk = pick ? t1 : t0;
-    if (k < 2 || !D.has_walls) {
-      tk %= nt[k];
-      if (tk < 0) tk += nt[k];
-      // the stencil of a short periodic axis may wrap onto the same tile twice
-      if (pick && tk == ((t0 % nt[k]) + nt[k]) % nt[k]) return;
-    } else if (tk < 0 || tk >= nt[k] || tk * TILE >= n[k]) {
-      return;  // beyond the lattice in z: those stencil nodes are skipped
-    }
-    t[k] = tk;
+    const bool up = (e >> k) & 1;
+    if (up ? !ax[k].ok1 : !ax[k].ok0) return;
+    t[k] = up ? ax[k].t1 : ax[k].t0;
   }
   claim_tile((t[2] * D.nty + t[1]) * D.ntx + t[0], tile_slot, slot_tile, nslots, slot_count,
              health, D.max_slots);
@@ -453,7 +566,8 @@ __device__ __forceinline__ void mark_tiles(const double p[3], int e, const Dims 
 template <typename real>
 __global__ void __launch_bounds__(256) interp_kernel(
     int nv, const StencilRec<real> *__restrict__ stencil, const int *__restrict__ tile_slot,
-    const real *__restrict__ Uslot, double *__restrict__ q, double *__restrict__ qdot,
+    const Vec4<real> *__restrict__ Uslot, double *__restrict__ q, double *__restrict__ qdot,
+    const double *__restrict__ xref, Vec4<real> *__restrict__ disp,
     double3 ub, double3 ut, Dims D, int *__restrict__ next_tile_slot,
     int *__restrict__ next_slot_tile, int *__restrict__ next_nslots, int *__restrict__ slot_count,
     int *__restrict__ health) {
@@ -463,11 +577,11 @@ __global__ void __launch_bounds__(256) interp_kernel(
   const bool valid = v < nv;
   real acc[3] = {0, 0, 0};
   if (valid) {
-    const StencilRec<real> &rec = stencil[v];
+    const StencilRec<real> rec = stencil[v];
     int Z = rec.base[2] + dz;
     if (!D.has_walls) Z = Z >= D.nz ? Z - D.nz : Z;
     if (Z >= 0 && Z < D.nz) {
-      const real wz = rec.w[2][dz];
+      const real wz = pick4(rec.w[2], dz);
       if (D.has_walls && (Z == 0 || Z == D.nz - 1)) {
         const double3 w = Z == 0 ? ub : ut;
         const real sxy = (rec.w[0][0] + rec.w[0][1] + rec.w[0][2] + rec.w[0][3]) *
@@ -499,11 +613,11 @@ __global__ void __launch_bounds__(256) interp_kernel(
               atomicOr(health, H_CAPACITY);
               continue;
             }
-            const real *Us = Uslot + (size_t)sidx * 3 * TILE_CELLS + (X[dx] & 3) + crow;
+            const Vec4<real> u = Uslot[(size_t)sidx * TILE_CELLS + (X[dx] & 3) + crow];
             const real w = rec.w[0][dx];
-            r3[0] += w * Us[0];
-            r3[1] += w * Us[TILE_CELLS];
-            r3[2] += w * Us[2 * TILE_CELLS];
+            r3[0] += w * u.x;
+            r3[1] += w * u.y;
+            r3[2] += w * u.z;
           }
           const real wyz = rec.w[1][dy] * wz;
           acc[0] += wyz * r3[0];
@@ -528,23 +642,49 @@ __global__ void __launch_bounds__(256) interp_kernel(
       }
       if (D.has_walls && (pn[2] - D.zb < 0.05 || D.zt - pn[2] < 0.05)) h |= H_WALL;
       if (h) atomicOr(health, h);
+      Vec4<real> d;
+      d.x = (real)(pn[0] - xref[3 * (size_t)v]);
+      d.y = (real)(pn[1] - xref[3 * (size_t)v + 1]);
+      d.z = (real)(pn[2] - xref[3 * (size_t)v + 2]);
+      d.w = real(0);
+      disp[v] = d;
     }
     if (next_tile_slot != nullptr && pn[0] == pn[0] && pn[1] == pn[1] && pn[2] == pn[2]) {
-      mark_tiles(pn, dz, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, health);
-      mark_tiles(pn, dz + 4, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, health);
+      AxisTiles ax[3];
+      ax[0] = axis_tiles(pn[0], D.ntx, D.inx, true);
+      ax[1] = axis_tiles(pn[1], D.nty, D.iny, true);
+      ax[2] = axis_tiles(pn[2], D.ntz, D.inz, !D.has_walls);
+      mark_tile(ax, dz, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, health);
+      mark_tile(ax, dz + 4, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, health);
     }
   }
 }
 
-// Standalone marking of the current positions (after setting vertices).
-__global__ void mark_kernel(int nv, const double *__restrict__ q, Dims D, int *tile_slot,
+// Standalone marking of the current positions (after setting vertices); also refreshes the
+// float displacement from the reference shape.
+template <typename real>
+__global__ void mark_kernel(int nv, const double *__restrict__ q, const double *__restrict__ xref,
+                            Vec4<real> *__restrict__ disp, Dims D, int *tile_slot,
                             int *slot_tile, int *nslots, int *slot_count, int *health) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = gid >> 3, e = gid & 7;
   if (v >= nv) return;
   const double p[3] = {q[3 * (size_t)v], q[3 * (size_t)v + 1], q[3 * (size_t)v + 2]};
-  if (p[0] == p[0] && p[1] == p[1] && p[2] == p[2])
-    mark_tiles(p, e, D, tile_slot, slot_tile, nslots, slot_count, health);
+  if (e == 0) {
+    Vec4<real> d;
+    d.x = (real)(p[0] - xref[3 * (size_t)v]);
+    d.y = (real)(p[1] - xref[3 * (size_t)v + 1]);
+    d.z = (real)(p[2] - xref[3 * (size_t)v + 2]);
+    d.w = real(0);
+    disp[v] = d;
+  }
+  if (p[0] == p[0] && p[1] == p[1] && p[2] == p[2]) {
+    AxisTiles ax[3];
+    ax[0] = axis_tiles(p[0], D.ntx, D.inx, true);
+    ax[1] = axis_tiles(p[1], D.nty, D.iny, true);
+    ax[2] = axis_tiles(p[2], D.ntz, D.inz, !D.has_walls);
+    mark_tile(ax, e, D, tile_slot, slot_tile, nslots, slot_count, health);
+  }
 }
 
 __global__ void clear_counts_kernel(const int *__restrict__ nslots, int *__restrict__ slot_count,
@@ -557,7 +697,8 @@ __global__ void clear_counts_kernel(const int *__restrict__ nslots, int *__restr
 
 template <typename real>
 __global__ void expand_force_kernel(const int *__restrict__ slot_tile, const int *__restrict__ nslots,
-                                    const real *__restrict__ Fslot, Dims D, double *__restrict__ F) {
+                                    const Vec4<real> *__restrict__ Fslot, Dims D,
+                                    double *__restrict__ F) {
   const int n = min(*nslots, D.max_slots);
   for (int b = blockIdx.x; b < n; b += gridDim.x) {
     const int t = slot_tile[b];
@@ -566,20 +707,48 @@ __global__ void expand_force_kernel(const int *__restrict__ slot_tile, const int
     const int X = tx * TILE + (c & 3), Y = ty * TILE + ((c >> 2) & 3), Z = tz * TILE + (c >> 4);
     if (Z >= D.nz) continue;
     const size_t node = ((size_t)Z * D.ny + Y) * D.nx + X;
-    for (int k = 0; k < 3; k++)
-      F[3 * node + k] = (double)Fslot[(size_t)b * 3 * TILE_CELLS + k * TILE_CELLS + c];
+    const Vec4<real> f = Fslot[(size_t)b * TILE_CELLS + c];
+    F[3 * node] = (double)f.x;
+    F[3 * node + 1] = (double)f.y;
+    F[3 * node + 2] = (double)f.z;
   }
 }
 
+// Nodal force of Eq. 16, phi - kV (V - V0)/V0 dV/dq, in double for read-back.
 template <typename real>
-__global__ void to_double_kernel(int n, const real *__restrict__ in, double *__restrict__ out) {
+__global__ void combine_forces_kernel(int nv, const Vec4<real> *__restrict__ phi,
+                                      const Vec4<real> *__restrict__ gvol,
+                                      const double *__restrict__ vol_partial, VolumeParams vp,
+                                      double *__restrict__ out) {
+  __shared__ double s_coef;
+  if (threadIdx.x < 32) {
+    const double coef = volume_coef(vol_partial, vp.vol_blocks, vp.V0, vp.kV, vp.volume_on, nullptr);
+    if (threadIdx.x == 0) s_coef = coef;
+  }
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (double)in[i];
+  if (i >= nv) return;
+  const real coef = (real)s_coef;
+  const Vec4<real> p = phi[i], g = gvol[i];
+  out[3 * (size_t)i] = (double)(p.x - coef * g.x);
+  out[3 * (size_t)i + 1] = (double)(p.y - coef * g.y);
+  out[3 * (size_t)i + 2] = (double)(p.z - coef * g.z);
 }
 
-__global__ void volume_sum_kernel(const double *__restrict__ part, int n, double *__restrict__ out) {
-  const double v = total_volume(part, n);
-  if (threadIdx.x == 0) *out = v;
+__global__ void volume_sum_kernel(const double *__restrict__ part, int n, double V0,
+                                  double *__restrict__ out) {
+  double V;
+  volume_coef(part, n, V0, 0.0, 0, &V);
+  if (threadIdx.x == 0) *out = V;
+}
+
+VolumeParams volume_params(const Ctx &c) {
+  VolumeParams vp;
+  vp.V0 = c.V0;
+  vp.kV = c.iface.kV;
+  vp.volume_on = c.iface.volume_force_on;
+  vp.vol_blocks = c.vol_blocks;
+  return vp;
 }
 
 template <typename real>
@@ -591,28 +760,21 @@ cudaError_t face_forces_t(Ctx &c, int reset, cudaStream_t st) {
   fp.eps48 = 48.0 * c.iface.eps;
   fp.xi = c.iface.xi;
   fp.wall_on = c.iface.wall_force_on;
-  fp.cx = c.centre[0];
-  fp.cy = c.centre[1];
-  fp.cz = c.centre[2];
   const int other = c.map ^ 1;
   face_kernel<real><<<c.vol_blocks, 256, 0, st>>>(
-      c.nf, c.faces, c.q, c.fref, (real *)c.fcontrib, (real *)c.fnorm, c.vol_partial, fp,
-      dims_of(c), c.tile_slot[other], c.slot_tile[other], c.counters + other, reset,
-      c.counters + 2);
+      c.nf, c.faces, (const Vec4<real> *)c.disp, c.fref, (const real *)c.fgeo,
+      (real *)c.fcontrib, (real *)c.fnorm, c.vol_partial, fp, dims_of(c), c.tile_slot[other],
+      c.slot_tile[other],
+      c.counters + other, reset, c.counters + 2);
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t vertex_forces_t(Ctx &c, int bin, cudaStream_t st) {
-  VertexParams vp;
-  vp.V0 = c.V0;
-  vp.kV = c.iface.kV;
-  vp.volume_on = c.iface.volume_force_on;
-  vp.vol_blocks = c.vol_blocks;
   vertex_kernel<real><<<(c.nv + 255) / 256, 256, 0, st>>>(
-      c.nv, c.vol_partial, vp, c.vf_start, c.vf_list, (const real *)c.fcontrib,
-      (const real *)c.fnorm, c.q, (real *)c.phi, (StencilRec<real> *)c.stencil, bin,
-      c.tile_slot[c.map], c.slot_count, c.bucket, c.overflow, c.counters + 2, c.counters + 3,
+      c.nv, c.vf_start, c.vf_list, (const real *)c.fcontrib, (const real *)c.fnorm, c.q,
+      (Vec4<real> *)c.phi, (Vec4<real> *)c.gvol, (StencilRec<real> *)c.stencil, bin, c.tile_slot[c.map],
+      c.slot_count, c.bucket, c.overflow, c.counters + 2, c.counters + 3,
       bin == 2 ? c.counters + (c.map ^ 1) : nullptr, dims_of(c));
   return cudaGetLastError();
 }
@@ -624,13 +786,15 @@ cudaError_t spread_t(Ctx &c, cudaStream_t st) {
   sort_buckets_kernel<<<sgrid, 256, 0, st>>>(c.counters + c.map, c.slot_count, c.bucket, c.max_slots);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int grid = c.sm_count * 16;
+  // persistent grid: enough resident blocks for the SMs the interface chain runs on
+  int grid = (c.ib_sms > 0 ? c.ib_sms : c.sm_count) * 12;
   if (grid * SPREAD_TILES > c.max_slots) grid = (c.max_slots + SPREAD_TILES - 1) / SPREAD_TILES;
   if (grid < 1) grid = 1;
   spread_kernel<real><<<grid, TILE_CELLS, 0, st>>>(
       c.tile_slot[c.map], c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.bucket,
-      c.overflow, c.counters + 2, (const StencilRec<real> *)c.stencil, (const real *)c.phi,
-      (real *)c.Fslot[c.map], dims_of(c));
+      c.overflow, c.counters + 2, (const StencilRec<real> *)c.stencil, (const Vec4<real> *)c.phi,
+      (const Vec4<real> *)c.gvol, c.vol_partial, volume_params(c), c.counters + 3,
+      (Vec4<real> *)c.Fslot[c.map], dims_of(c));
   return cudaGetLastError();
 }
 
@@ -639,10 +803,10 @@ cudaError_t interp_t(Ctx &c, cudaStream_t st) {
   const int other = c.map ^ 1;
   const long threads = 4L * c.nv;
   interp_kernel<real><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-      c.nv, (const StencilRec<real> *)c.stencil, c.tile_slot[c.map], (const real *)c.Uslot, c.q,
-      c.qdot, make_double3(c.ub[0], c.ub[1], c.ub[2]), make_double3(c.ut[0], c.ut[1], c.ut[2]),
-      dims_of(c), c.tile_slot[other], c.slot_tile[other], c.counters + other, c.slot_count,
-      c.counters + 3);
+      c.nv, (const StencilRec<real> *)c.stencil, c.tile_slot[c.map], (const Vec4<real> *)c.Uslot,
+      c.q, c.qdot, c.xref, (Vec4<real> *)c.disp, make_double3(c.ub[0], c.ub[1], c.ub[2]),
+      make_double3(c.ut[0], c.ut[1], c.ut[2]), dims_of(c), c.tile_slot[other],
+      c.slot_tile[other], c.counters + other, c.slot_count, c.counters + 3);
   return cudaGetLastError();
 }
 
@@ -674,9 +838,15 @@ cudaError_t launch_interpolate_advect(Ctx &c, cudaStream_t s) {
 
 cudaError_t launch_mark(Ctx &c) {
   const long threads = 8L * c.nv;
-  mark_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.stream>>>(
-      c.nv, c.q, dims_of(c), c.tile_slot[c.map], c.slot_tile[c.map], c.counters + c.map,
-      c.slot_count, c.counters + 3);
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  if (c.precision == IBLB_FP64)
+    mark_kernel<double><<<blocks, 256, 0, c.stream>>>(
+        c.nv, c.q, c.xref, (Vec4<double> *)c.disp, dims_of(c), c.tile_slot[c.map],
+        c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.counters + 3);
+  else
+    mark_kernel<float><<<blocks, 256, 0, c.stream>>>(
+        c.nv, c.q, c.xref, (Vec4<float> *)c.disp, dims_of(c), c.tile_slot[c.map],
+        c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.counters + 3);
   return cudaGetLastError();
 }
 
@@ -694,24 +864,28 @@ cudaError_t launch_expand_force(Ctx &c, double *F_dev) {
   if (grid < 1) grid = 1;
   if (c.precision == IBLB_FP64)
     expand_force_kernel<double><<<grid, TILE_CELLS, 0, c.stream>>>(
-        c.slot_tile[c.map], c.counters + c.map, (const double *)c.Fslot[c.map], dims_of(c), F_dev);
+        c.slot_tile[c.map], c.counters + c.map, (const Vec4<double> *)c.Fslot[c.map], dims_of(c), F_dev);
   else
     expand_force_kernel<float><<<grid, TILE_CELLS, 0, c.stream>>>(
-        c.slot_tile[c.map], c.counters + c.map, (const float *)c.Fslot[c.map], dims_of(c), F_dev);
+        c.slot_tile[c.map], c.counters + c.map, (const Vec4<float> *)c.Fslot[c.map], dims_of(c), F_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_phi_to_double(Ctx &c, double *phi_dev) {
-  const int n = 3 * c.nv;
+  const int blocks = (c.nv + 255) / 256;
   if (c.precision == IBLB_FP64)
-    to_double_kernel<double><<<(n + 255) / 256, 256, 0, c.stream>>>(n, (const double *)c.phi, phi_dev);
+    combine_forces_kernel<double><<<blocks, 256, 0, c.stream>>>(
+        c.nv, (const Vec4<double> *)c.phi, (const Vec4<double> *)c.gvol, c.vol_partial,
+        volume_params(c), phi_dev);
   else
-    to_double_kernel<float><<<(n + 255) / 256, 256, 0, c.stream>>>(n, (const float *)c.phi, phi_dev);
+    combine_forces_kernel<float><<<blocks, 256, 0, c.stream>>>(
+        c.nv, (const Vec4<float> *)c.phi, (const Vec4<float> *)c.gvol, c.vol_partial,
+        volume_params(c), phi_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_volume(Ctx &c, double *V_dev) {
-  volume_sum_kernel<<<1, 32, 0, c.stream>>>(c.vol_partial, c.vol_blocks, V_dev);
+  volume_sum_kernel<<<1, 32, 0, c.stream>>>(c.vol_partial, c.vol_blocks, c.V0, V_dev);
   return cudaGetLastError();
 }
 

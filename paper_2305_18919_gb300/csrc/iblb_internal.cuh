@@ -44,6 +44,13 @@ constexpr int BUCKET_CAP = 64;
 // Health word bits (read back by iblb_step).
 constexpr int H_NAN = 1, H_FAST = 2, H_WALL = 4, H_VOLUME = 8, H_CAPACITY = 16;
 
+// Force and velocity blocks of the active tiles are [slot][64 nodes] of these: x, y, z and one
+// pad, so that each node is one aligned vector access.
+template <typename real>
+struct alignas(4 * sizeof(real)) Vec4 {
+  real x, y, z, w;
+};
+
 // Per-vertex stencil record written by the vertex kernel and read by spreading and
 // interpolation: base node (floor(q) - 1, x/y wrapped), the 3x4 one-dimensional weights.
 template <typename real>
@@ -63,8 +70,11 @@ struct Ctx {
   int cur = 0;                      // f[cur] holds the state
   int fresh = 1;                    // state is post-streaming (no collision done yet)
   int have_force = 0;               // a spread field exists (for read_fields)
-  cudaStream_t stream = nullptr;   // caller's stream: lattice kernels and all transfers
+  cudaStream_t stream = nullptr;   // caller's stream: transfers and read-back kernels
+  cudaStream_t ls = nullptr;       // stream of the stream-collide passes of iblb_step
   cudaStream_t ib = nullptr;       // library stream: the interface chain of each step
+  void *green[2] = {nullptr, nullptr};  // SM partitions (CUgreenCtx): [0] interface, [1] lattice
+  int ib_sms = 0;                  // SMs of the interface partition (0: no partition)
   cudaEvent_t ev_force = nullptr;  // spread force of the step is ready (recorded on ib)
   cudaEvent_t ev_coll = nullptr;   // post-collision populations of the step are complete
   cudaEvent_t ev_sync = nullptr;   // general cross-stream join
@@ -78,8 +88,8 @@ struct Ctx {
   int *slot_count = nullptr;               // [max_slots] vertices in each source bucket
   int *bucket = nullptr;                   // [max_slots][BUCKET_CAP]
   int *overflow = nullptr;                 // [nv] vertices not fitting in their bucket
-  void *Fslot[2] = {nullptr, nullptr};     // per map: [max_slots][3][64] force density
-  void *Uslot = nullptr;                   // [max_slots][3][64] velocity
+  void *Fslot[2] = {nullptr, nullptr};     // per map: [max_slots][64] Vec4 force density
+  void *Uslot = nullptr;                   // [max_slots][64] Vec4 velocity
   int map = 0;                             // tile map of the current vertex positions
   // mesh
   int nv = 0, nf = 0;
@@ -87,13 +97,18 @@ struct Ctx {
   double *qdot = nullptr;    // [nv][3]
   int *faces = nullptr;      // [nf][3]
   double *fref = nullptr;    // [nf][4] reference metric inverse (H11, H12, H22) and A0
+  double *xref = nullptr;    // [nv][3] reference vertex positions
+  void *disp = nullptr;      // [nv] Vec4: q - xref in the population type (kept by K2)
+  void *fgeo = nullptr;      // [nf][12] reference edges A, B, X0 - c, heights above the walls
   int *vf_start = nullptr;   // [nv+1] CSR vertex -> (face*3 + corner)
   int *vf_list = nullptr;    // [3 nf]
   void *fcontrib = nullptr;  // [nf][3 corners][3]: strain + wall force per corner
   void *fnorm = nullptr;     // [nf][3]: (a x b)/6, the face's volume gradient at each corner
-  double *vol_partial = nullptr;  // [vol_blocks]
+  double *vol_partial = nullptr;  // [vol_blocks] partial sums of V - V0 (one per face block)
   int vol_blocks = 0;
-  void *phi = nullptr;       // [nv][3] nodal forces of the last evaluation
+  void *phi = nullptr;       // [nv] Vec4: strain + wall part of the nodal force (Eq. 16 without
+                             //   the volume term, which is applied where the force is used)
+  void *gvol = nullptr;      // [nv] Vec4: dV/dq of each vertex
   void *stencil = nullptr;   // [nv] StencilRec
   double V0 = 0.0, centre[3] = {0, 0, 0};
   iblb_iface_params iface{};

@@ -59,18 +59,21 @@ __device__ __forceinline__ void pull(const real *__restrict__ fp, const LatParam
   }
   const bool wall_below = P.has_walls && zm == 0;
   const bool wall_above = P.has_walls && zp == P.nz - 1;
-  const size_t n = ((size_t)z * P.ny + y) * P.nx + x;
+  const size_t plane = (size_t)P.nx * P.ny;
+  // source offsets along each axis, indexed by 1 - c (c = +1 -> minus side, c = -1 -> plus side)
+  const size_t zo[3] = {(size_t)zm * plane, (size_t)z * plane, (size_t)zp * plane};
+  const size_t yo[3] = {(size_t)ym * P.nx, (size_t)y * P.nx, (size_t)yp * P.nx};
+  const int xo[3] = {xm, x, xp};
+  const size_t n = zo[1] + yo[1] + x;
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    const int sx = cx(i) > 0 ? xm : (cx(i) < 0 ? xp : x);
-    const int sy = cy(i) > 0 ? ym : (cy(i) < 0 ? yp : y);
-    const int sz = cz(i) > 0 ? zm : (cz(i) < 0 ? zp : z);
+    const real *fi = fp + (size_t)i * P.ncell;
     if (cz(i) > 0 && wall_below) {
       f[i] = fp[(size_t)opp(i) * P.ncell + n] + P.wb[i];
     } else if (cz(i) < 0 && wall_above) {
       f[i] = fp[(size_t)opp(i) * P.ncell + n] + P.wt[i];
     } else {
-      f[i] = fp[(size_t)i * P.ncell + ((size_t)sz * P.ny + sy) * P.nx + sx];
+      f[i] = fi[zo[1 - cz(i)] + yo[1 - cy(i)] + xo[1 - cx(i)]];
     }
   }
 }
@@ -78,7 +81,7 @@ __device__ __forceinline__ void pull(const real *__restrict__ fp, const LatParam
 // Interface force density of node (x, y, z) from the active-tile table (0 if inactive).
 template <typename real>
 __device__ __forceinline__ void tile_force(const int *__restrict__ tile_slot,
-                                           const real *__restrict__ Fslot,
+                                           const Vec4<real> *__restrict__ Fslot,
                                            const LatParams<real> &P, int x, int y, int z,
                                            real F[3]) {
   F[0] = P.g[0];
@@ -89,27 +92,30 @@ __device__ __forceinline__ void tile_force(const int *__restrict__ tile_slot,
   const int s = tile_slot[t];
   if (s >= 0) {
     const int cell = (x & 3) + 4 * (y & 3) + 16 * (z & 3);
-    const real *Fs = Fslot + (size_t)s * 3 * TILE_CELLS + cell;
-    F[0] += Fs[0];
-    F[1] += Fs[TILE_CELLS];
-    F[2] += Fs[2 * TILE_CELLS];
+    const Vec4<real> Fs = Fslot[(size_t)s * TILE_CELLS + cell];
+    F[0] += Fs.x;
+    F[1] += Fs.y;
+    F[2] += Fs.z;
   }
 }
 
 // BGK collision with Guo forcing (Eqs. 9-10) of one node's shifted populations f, storing
-// the post-collision populations at node n of fout.
-template <typename real>
-__device__ __forceinline__ void collide_store(const real f[Q], const real F[3],
-                                              real *__restrict__ fout, size_t n,
-                                              const LatParams<real> &P) {
+// the post-collision populations at node n of fout. Opposite directions i, i+1 (i odd) share
+// c.u and c.F up to sign, so each pair is computed from its symmetric and antisymmetric parts:
+//   f^eq - w rho0 = w [drho + rho (4.5 (c.u)^2 - 1.5 u^2)] +- w rho 3 (c.u)      (Eq. 10)
+//   S = w (1 - 1/2tau) [9 (c.F)(c.u) - 3 u.F] +- w (1 - 1/2tau) 3 (c.F)          (Eq. 9)
+// With FORCE false the force is zero and the Guo terms vanish.
+template <typename real, bool FORCE>
+__device__ __forceinline__ void collide(real f[Q], const real F[3], const LatParams<real> &P) {
   // moments: rho = rho0 + sum f~, j = sum c f~ (the rest-state part carries no momentum)
-  real drho = 0, jx = 0, jy = 0, jz = 0;
+  real drho = f[0], jx = 0, jy = 0, jz = 0;
 #pragma unroll
-  for (int i = 0; i < Q; i++) {
-    drho += f[i];
-    if (cx(i)) jx += cx(i) > 0 ? f[i] : -f[i];
-    if (cy(i)) jy += cy(i) > 0 ? f[i] : -f[i];
-    if (cz(i)) jz += cz(i) > 0 ? f[i] : -f[i];
+  for (int i = 1; i < Q; i += 2) {
+    drho += f[i] + f[i + 1];
+    const real d = f[i] - f[i + 1];
+    if (cx(i)) jx += cx(i) > 0 ? d : -d;
+    if (cy(i)) jy += cy(i) > 0 ? d : -d;
+    if (cz(i)) jz += cz(i) > 0 ? d : -d;
   }
   // rho = rho0 + drho is never rounded as a whole: 1/rho carries the rounding remainder of
   // the sum (Fast2Sum, |rho0| >= |drho|), and rho X is expanded as rho0 X + drho X
@@ -117,46 +123,138 @@ __device__ __forceinline__ void collide_store(const real f[Q], const real F[3],
   const real rho_lo = (P.rho0 - rho_hi) + drho;
   const real r1 = real(1) / rho_hi;
   const real inv_rho = r1 * (real(1) - rho_lo * r1);
-  const real ux = (jx + real(0.5) * F[0]) * inv_rho;
-  const real uy = (jy + real(0.5) * F[1]) * inv_rho;
-  const real uz = (jz + real(0.5) * F[2]) * inv_rho;
+  real ux = jx, uy = jy, uz = jz;
+  if (FORCE) {
+    ux += real(0.5) * F[0];
+    uy += real(0.5) * F[1];
+    uz += real(0.5) * F[2];
+  }
+  ux *= inv_rho;
+  uy *= inv_rho;
+  uz *= inv_rho;
   const real uu15 = real(1.5) * (ux * ux + uy * uy + uz * uz);
-  const real uF3 = real(3) * (ux * F[0] + uy * F[1] + uz * F[2]);
+  const real om = P.omega;
+  real uF3 = 0;
+  if (FORCE) uF3 = real(3) * (ux * F[0] + uy * F[1] + uz * F[2]);
+  {  // rest population
+    const real w = (real)wgt(0);
+    const real feq = w * (drho - P.rho0 * uu15 - drho * uu15);
+    real out = f[0] + om * (feq - f[0]);
+    if (FORCE) out -= w * P.guo * uF3;
+    f[0] = out;
+  }
 #pragma unroll
-  for (int i = 0; i < Q; i++) {
+  for (int i = 1; i < Q; i += 2) {
     const real w = (real)wgt(i);
     const real cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-    const real cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
-    // f^eq - w rho0 = w [drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2)]   (Eq. 10)
-    const real X = real(3) * cu + real(4.5) * cu * cu - uu15;
-    const real feq = w * (drho + P.rho0 * X + drho * X);
-    // Guo source: w (1 - 1/2tau) [3 (c - u).F + 9 (c.F)(c.u)]         (Eq. 9)
-    const real S = w * P.guo * (real(3) * cF - uF3 + real(9) * cF * cu);
-    fout[(size_t)i * P.ncell + n] = f[i] - P.omega * (f[i] - feq) + S;
+    const real xs = real(4.5) * cu * cu - uu15;
+    const real xa = real(3) * cu;
+    const real sym = w * (drho + P.rho0 * xs + drho * xs);
+    const real asym = w * (P.rho0 * xa + drho * xa);
+    real a = f[i] + om * (sym + asym - f[i]);
+    real b = f[i + 1] + om * (sym - asym - f[i + 1]);
+    if (FORCE) {
+      const real cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
+      const real ssym = w * P.guo * (real(9) * cF * cu - uF3);
+      const real sasym = w * P.guo * real(3) * cF;
+      a += ssym + sasym;
+      b += ssym - sasym;
+    }
+    f[i] = a;
+    f[i + 1] = b;
   }
 }
 
-// K1: fused stream-collide of every fluid node, one thread per node, with the uniform body
-// force only. The nodes of active interface tiles are collided again by K1t with their
-// interface force, so this pass does not wait for the interface chain of the step.
-template <typename real, bool FIRST>
+template <typename real, bool FORCE>
+__device__ __forceinline__ void collide_store(real f[Q], const real F[3], real *__restrict__ fout,
+                                              size_t n, const LatParams<real> &P) {
+  collide<real, FORCE>(f, F, P);
+#pragma unroll
+  for (int i = 0; i < Q; i++) fout[(size_t)i * P.ncell + n] = f[i];
+}
+
+template <typename real>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using T = float2;
+};
+template <>
+struct Vec2<double> {
+  using T = double2;
+};
+
+// K1: fused stream-collide of every fluid node with the uniform body force only (FORCE: the
+// body force is non-zero). The nodes of active interface tiles are collided again by K1t with
+// their interface force, so this pass does not wait for the interface chain of the step.
+// Each thread owns the two nodes (x0, x0 + 1), x0 even: populations that do not move along x
+// and every store are one aligned 2-wide access, and the address arithmetic is shared.
+template <typename real, bool FIRST, bool FORCE>
 __global__ void __launch_bounds__(128) stream_collide_kernel(const real *__restrict__ fin,
                                                              real *__restrict__ fout,
                                                              const LatParams<real> P, int z0) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  using V2 = typename Vec2<real>::T;
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y;
   const int z = blockIdx.z + z0;
-  if (x >= P.nx) return;
-  const size_t n = ((size_t)z * P.ny + y) * P.nx + x;
-  real f[Q];
+  if (x0 >= P.nx) return;
+  const size_t plane = (size_t)P.nx * P.ny;
+  const size_t n = (size_t)z * plane + (size_t)y * P.nx + x0;
+  real a[Q], b[Q];  // populations of nodes x0 and x0 + 1
   if (FIRST) {
 #pragma unroll
-    for (int i = 0; i < Q; i++) f[i] = fin[(size_t)i * P.ncell + n];
+    for (int i = 0; i < Q; i++) {
+      const V2 v = *reinterpret_cast<const V2 *>(fin + (size_t)i * P.ncell + n);
+      a[i] = v.x;
+      b[i] = v.y;
+    }
   } else {
-    pull(fin, P, x, y, z, f);
+    const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;       // source of node x0 for c_x = +1
+    const int xp = x0 + 2 == P.nx ? 0 : x0 + 2;       // source of node x0 + 1 for c_x = -1
+    const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
+    int zm = z - 1, zp = z + 1;
+    if (!P.has_walls) {
+      zm = z == 0 ? P.nz - 1 : zm;
+      zp = z == P.nz - 1 ? 0 : zp;
+    }
+    const bool wall_below = P.has_walls && zm == 0;
+    const bool wall_above = P.has_walls && zp == P.nz - 1;
+    const size_t zo[3] = {(size_t)zm * plane, (size_t)z * plane, (size_t)zp * plane};
+    const size_t yo[3] = {(size_t)ym * P.nx, (size_t)y * P.nx, (size_t)yp * P.nx};
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      if ((cz(i) > 0 && wall_below) || (cz(i) < 0 && wall_above)) {
+        // half-way bounce-back: opposite post-collision population of the same nodes
+        const V2 v = *reinterpret_cast<const V2 *>(fin + (size_t)opp(i) * P.ncell + n);
+        const real wall = cz(i) > 0 ? P.wb[i] : P.wt[i];
+        a[i] = v.x + wall;
+        b[i] = v.y + wall;
+        continue;
+      }
+      const real *row = fin + (size_t)i * P.ncell + zo[1 - cz(i)] + yo[1 - cy(i)];
+      if (cx(i) == 0) {
+        const V2 v = *reinterpret_cast<const V2 *>(row + x0);
+        a[i] = v.x;
+        b[i] = v.y;
+      } else if (cx(i) > 0) {
+        a[i] = row[xm];
+        b[i] = row[x0];
+      } else {
+        a[i] = row[x0 + 1];
+        b[i] = row[xp];
+      }
+    }
   }
   const real F[3] = {P.g[0], P.g[1], P.g[2]};
-  collide_store(f, F, fout, n, P);
+  collide<real, FORCE>(a, F, P);
+  collide<real, FORCE>(b, F, P);
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    V2 v;
+    v.x = a[i];
+    v.y = b[i];
+    *reinterpret_cast<V2 *>(fout + (size_t)i * P.ncell + n) = v;
+  }
 }
 
 // K1t: stream-collide of the fluid nodes of the active tiles with body + interface force,
@@ -165,8 +263,8 @@ __global__ void __launch_bounds__(128) stream_collide_kernel(const real *__restr
 template <typename real, bool FIRST>
 __global__ void __launch_bounds__(64) stream_collide_tiles_kernel(
     const real *__restrict__ fin, real *__restrict__ fout, const int *__restrict__ slot_tile,
-    const int *__restrict__ nslots_ptr, const real *__restrict__ Fslot, const LatParams<real> P,
-    int max_slots) {
+    const int *__restrict__ nslots_ptr, const Vec4<real> *__restrict__ Fslot,
+    const LatParams<real> P, int max_slots) {
   const int nslots = min(*nslots_ptr, max_slots);
   const int cell = threadIdx.x;
   for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
@@ -183,9 +281,9 @@ __global__ void __launch_bounds__(64) stream_collide_tiles_kernel(
     } else {
       pull(fin, P, x, y, z, f);
     }
-    const real *Fs = Fslot + (size_t)s * 3 * TILE_CELLS + cell;
-    const real F[3] = {P.g[0] + Fs[0], P.g[1] + Fs[TILE_CELLS], P.g[2] + Fs[2 * TILE_CELLS]};
-    collide_store(f, F, fout, n, P);
+    const Vec4<real> Fs = Fslot[(size_t)s * TILE_CELLS + cell];
+    const real F[3] = {P.g[0] + Fs.x, P.g[1] + Fs.y, P.g[2] + Fs.z};
+    collide_store<real, true>(f, F, fout, n, P);
   }
 }
 
@@ -195,8 +293,8 @@ template <typename real>
 __global__ void __launch_bounds__(64) shell_velocity_kernel(const real *__restrict__ fpost,
                                                             const int *__restrict__ slot_tile,
                                                             const int *__restrict__ nslots_ptr,
-                                                            const real *__restrict__ Fslot,
-                                                            real *__restrict__ Uslot,
+                                                            const Vec4<real> *__restrict__ Fslot,
+                                                            Vec4<real> *__restrict__ Uslot,
                                                             const LatParams<real> P, real ubx,
                                                             real uby, real ubz, real utx,
                                                             real uty, real utz, int max_slots) {
@@ -224,26 +322,30 @@ __global__ void __launch_bounds__(64) shell_velocity_kernel(const real *__restri
           j[1] += cy(i) * f[i];
           j[2] += cz(i) * f[i];
         }
-        const real *Fs = Fslot + (size_t)s * 3 * TILE_CELLS + cell;
+        const Vec4<real> Fs = Fslot[(size_t)s * TILE_CELLS + cell];
+        const real Fk[3] = {Fs.x, Fs.y, Fs.z};
         const real rho_hi = P.rho0 + drho;
         const real rho_lo = (P.rho0 - rho_hi) + drho;
         const real r1 = real(1) / rho_hi;
         const real inv_rho = r1 * (real(1) - rho_lo * r1);
         for (int k = 0; k < 3; k++)
-          u[k] = (j[k] + real(0.5) * (P.g[k] + Fs[k * TILE_CELLS])) * inv_rho;
+          u[k] = (j[k] + real(0.5) * (P.g[k] + Fk[k])) * inv_rho;
       }
     }
-    real *Us = Uslot + (size_t)s * 3 * TILE_CELLS + cell;
-    Us[0] = u[0];
-    Us[TILE_CELLS] = u[1];
-    Us[2 * TILE_CELLS] = u[2];
+    Vec4<real> uv;
+    uv.x = u[0];
+    uv.y = u[1];
+    uv.z = u[2];
+    uv.w = real(0);
+    Uslot[(size_t)s * TILE_CELLS + cell] = uv;
   }
 }
 
 // rho and u of every node of the current post-streaming state (read-back, not on the step).
 template <typename real>
 __global__ void fields_kernel(const real *__restrict__ fstate, int fresh,
-                              const int *__restrict__ tile_slot, const real *__restrict__ Fslot,
+                              const int *__restrict__ tile_slot,
+                              const Vec4<real> *__restrict__ Fslot,
                               const LatParams<real> P, double3 ub, double3 ut, double rho0,
                               double *__restrict__ rho_out, double *__restrict__ u_out) {
   const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -318,32 +420,37 @@ cudaError_t stream_collide_t(Ctx &c, int first, cudaStream_t st) {
   const LatParams<real> P = lat_params<real>(c);
   const int z0 = c.has_walls ? 1 : 0;
   const int nzf = c.has_walls ? c.nz - 2 : c.nz;
-  const int bx = c.nx < 128 ? c.nx : 128;
-  dim3 grid((c.nx + bx - 1) / bx, c.ny, nzf);
+  const int half = c.nx / 2;  // two nodes per thread along x
+  const int bx = half < 128 ? half : 128;
+  dim3 grid((half + bx - 1) / bx, c.ny, nzf);
   const real *fin = (const real *)c.f[c.cur];
   real *fout = (real *)c.f[c.cur ^ 1];
-  if (first)
-    stream_collide_kernel<real, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
-  else
-    stream_collide_kernel<real, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+  const bool force = c.g[0] != 0.0 || c.g[1] != 0.0 || c.g[2] != 0.0;
+  if (first) {
+    if (force) stream_collide_kernel<real, true, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    else stream_collide_kernel<real, true, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+  } else {
+    if (force) stream_collide_kernel<real, false, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    else stream_collide_kernel<real, false, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+  }
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t stream_collide_tiles_t(Ctx &c, int first, cudaStream_t st) {
   const LatParams<real> P = lat_params<real>(c);
-  int grid = c.sm_count * 16;
+  int grid = c.sm_count * 32;  // one tile per block for up to ~4900 active tiles
   if (grid > c.max_slots) grid = c.max_slots;
   if (grid < 1) grid = 1;
   const real *fin = (const real *)c.f[c.cur];
   real *fout = (real *)c.f[c.cur ^ 1];
   if (first)
     stream_collide_tiles_kernel<real, true><<<grid, TILE_CELLS, 0, st>>>(
-        fin, fout, c.slot_tile[c.map], c.counters + c.map, (const real *)c.Fslot[c.map], P,
+        fin, fout, c.slot_tile[c.map], c.counters + c.map, (const Vec4<real> *)c.Fslot[c.map], P,
         c.max_slots);
   else
     stream_collide_tiles_kernel<real, false><<<grid, TILE_CELLS, 0, st>>>(
-        fin, fout, c.slot_tile[c.map], c.counters + c.map, (const real *)c.Fslot[c.map], P,
+        fin, fout, c.slot_tile[c.map], c.counters + c.map, (const Vec4<real> *)c.Fslot[c.map], P,
         c.max_slots);
   return cudaGetLastError();
 }
@@ -351,12 +458,12 @@ cudaError_t stream_collide_tiles_t(Ctx &c, int first, cudaStream_t st) {
 template <typename real>
 cudaError_t shell_velocity_t(Ctx &c, cudaStream_t st) {
   const LatParams<real> P = lat_params<real>(c);
-  int grid = c.sm_count * 16;
+  int grid = c.sm_count * 32;
   if (grid > c.max_slots) grid = c.max_slots;
   if (grid < 1) grid = 1;
   shell_velocity_kernel<real><<<grid, TILE_CELLS, 0, st>>>(
-      (const real *)c.f[c.cur], c.slot_tile[c.map], c.counters + c.map, (const real *)c.Fslot[c.map],
-      (real *)c.Uslot, P, (real)c.ub[0], (real)c.ub[1], (real)c.ub[2], (real)c.ut[0],
+      (const real *)c.f[c.cur], c.slot_tile[c.map], c.counters + c.map,
+      (const Vec4<real> *)c.Fslot[c.map], (Vec4<real> *)c.Uslot, P, (real)c.ub[0], (real)c.ub[1], (real)c.ub[2], (real)c.ut[0],
       (real)c.ut[1], (real)c.ut[2], c.max_slots);
   return cudaGetLastError();
 }
@@ -385,11 +492,11 @@ cudaError_t launch_fields(Ctx &c, double *rho_dev, double *u_dev) {
   const int *ts = (c.nv && c.have_force) ? c.tile_slot[c.map ^ 1] : nullptr;
   if (c.precision == IBLB_FP64) {
     fields_kernel<double><<<blocks, 256, 0, c.stream>>>(
-        (const double *)c.f[c.cur], c.fresh, ts, (const double *)c.Fslot[c.map ^ 1], lat_params<double>(c),
+        (const double *)c.f[c.cur], c.fresh, ts, (const Vec4<double> *)c.Fslot[c.map ^ 1], lat_params<double>(c),
         ub, ut, c.rho0, rho_dev, u_dev);
   } else {
     fields_kernel<float><<<blocks, 256, 0, c.stream>>>(
-        (const float *)c.f[c.cur], c.fresh, ts, (const float *)c.Fslot[c.map ^ 1], lat_params<float>(c), ub,
+        (const float *)c.f[c.cur], c.fresh, ts, (const Vec4<float> *)c.Fslot[c.map ^ 1], lat_params<float>(c), ub,
         ut, c.rho0, rho_dev, u_dev);
   }
   return cudaGetLastError();

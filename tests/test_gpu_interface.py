@@ -30,7 +30,11 @@ def test_nodal_forces_and_volume(cls, precision):
     assert rel_l2(gpu.forces(), phi_ref) < TOL[precision]
     V, V0 = gpu.volume()
     Vr, V0r = ref.volume()
-    assert abs(V0 - V0r) < 1e-12 * V0r and abs(V - Vr) < 1e-12 * Vr
+    assert abs(V0 - V0r) < 1e-12 * V0r
+    # V = V0 + sum of the per-face changes: double in FP64; in FP32 the changes are float, which
+    # leaves (V - Vr)/V0, the error of the volume-force coefficient, near 1e-9
+    tol_V = 1e-12 * Vr if precision == "fp64" else 1e-8 * Vr
+    assert abs(V - Vr) < tol_V
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
