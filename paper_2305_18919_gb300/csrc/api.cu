@@ -324,9 +324,10 @@ void iblb_destroy(iblb_ctx *h) {
     dfree(c.f[b]);
     dfree(c.tile_slot[b]);
     dfree(c.slot_tile[b]);
+    dfree(c.out_src[b]);
     dfree(c.Fslot[b]);
   }
-  dfree(c.counters); dfree(c.slot_count); dfree(c.bucket); dfree(c.overflow); dfree(c.Uslot);
+  dfree(c.counters); dfree(c.slot_count); dfree(c.src_index); dfree(c.Rslot); dfree(c.bucket); dfree(c.overflow); dfree(c.Uslot);
   dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.xref); dfree(c.fgeo); dfree(c.disp); dfree(c.vf_start); dfree(c.vf_list);
   dfree(c.fcontrib); dfree(c.fnorm); dfree(c.vol_partial); dfree(c.phi); dfree(c.gvol); dfree(c.stencil);
   dfree(c.dscratch);
@@ -415,10 +416,14 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
   for (int b = 0; b < 2; b++) {
     CUDA_TRY(c, dalloc(&c.tile_slot[b], c.ntiles));
     CUDA_TRY(c, dalloc(&c.slot_tile[b], (size_t)c.max_slots));
+    CUDA_TRY(c, dalloc(&c.out_src[b], (size_t)8 * c.max_slots));
     CUDA_TRY(c, dalloc_bytes(&c.Fslot[b], (size_t)c.max_slots * 4 * iblb::TILE_CELLS * rs));
     CUDA_TRY(c, cudaMemsetAsync(c.tile_slot[b], 0xff, c.ntiles * sizeof(int), c.stream));
   }
   CUDA_TRY(c, dalloc(&c.slot_count, (size_t)c.max_slots));
+  CUDA_TRY(c, dalloc(&c.src_index, (size_t)c.max_slots));
+  c.max_sources = nv < c.max_slots ? nv : c.max_slots;  // a source tile holds >= 1 vertex base
+  CUDA_TRY(c, dalloc_bytes(&c.Rslot, (size_t)c.max_sources * 343 * 4 * rs));
   CUDA_TRY(c, dalloc(&c.bucket, (size_t)c.max_slots * iblb::BUCKET_CAP));
   CUDA_TRY(c, dalloc(&c.overflow, (size_t)nv));
   CUDA_TRY(c, dalloc_bytes(&c.Uslot, (size_t)c.max_slots * 4 * iblb::TILE_CELLS * rs));

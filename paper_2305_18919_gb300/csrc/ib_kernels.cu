@@ -169,7 +169,10 @@ __global__ void __launch_bounds__(256) face_kernel(
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (threadIdx.x == 0) vol_partial[blockIdx.x] = v;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *ovf_count = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ovf_count[0] = 0;  // overflow list length
+    ovf_count[2] = 0;  // number of source tiles (counters[4])
+  }
   if (reset) {
     const int n_other = min(*other_nslots, D.max_slots);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_other; s += gridDim.x * blockDim.x)
@@ -219,7 +222,8 @@ __global__ void __launch_bounds__(256) vertex_kernel(
     const double *__restrict__ q, Vec4<real> *__restrict__ phi, Vec4<real> *__restrict__ gvol,
     StencilRec<real> *__restrict__ stencil, int bin, const int *__restrict__ tile_slot,
     int *__restrict__ slot_count, int *__restrict__ bucket, int *__restrict__ overflow,
-    int *__restrict__ ovf_count, int *__restrict__ health, int *__restrict__ zero_counter, Dims D) {
+    int *__restrict__ ovf_count, int *__restrict__ src_index, int *__restrict__ nsources,
+    int *__restrict__ health, int *__restrict__ zero_counter, Dims D) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (blockIdx.x == 0 && threadIdx.x == 0 && zero_counter) *zero_counter = 0;
   if (i >= nv) return;
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(256) vertex_kernel(
     return;
   }
   const int rank = atomicAdd(&slot_count[s], 1);
+  if (rank == 0) src_index[s] = atomicAdd(nsources, 1);  // first vertex: the tile gets a region
   if (rank < BUCKET_CAP) {
     bucket[(size_t)s * BUCKET_CAP + rank] = i;
   } else {
@@ -273,18 +278,85 @@ __global__ void __launch_bounds__(256) vertex_kernel(
   }
 }
 
-// K4a: sort every source bucket of the current map by vertex index (one warp per bucket,
-// rank by comparison; bucket sizes are at most 64), so that spreading sums in an order that
-// does not depend on the order in which the vertex kernel filled the buckets.
-__global__ void __launch_bounds__(256) sort_buckets_kernel(const int *__restrict__ nslots_ptr,
-                                                           const int *__restrict__ slot_count,
-                                                           int *__restrict__ bucket, int max_slots) {
-  const int nslots = min(*nslots_ptr, max_slots);
-  const int lane = threadIdx.x & 31;
-  const int warps = gridDim.x * (blockDim.x >> 5);
-  for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nslots; s += warps) {
-    const int n = min(slot_count[s], BUCKET_CAP);
-    int *bk = bucket + (size_t)s * BUCKET_CAP;
+struct VolumeParams {
+  double V0, kV;
+  int volume_on, vol_blocks;
+};
+
+// Spreading works on regions: the stencils of the vertices binned in a source tile S (base
+// node in S) cover the 7x7x7 nodes S_lo .. S_lo + 6.
+constexpr int REGION = 7;
+constexpr int REGION_NODES = REGION * REGION * REGION;
+// Source tiles per block of K4a (shared memory per warp: the region and the staged records).
+template <typename real>
+struct SrcWarps {
+  static constexpr int value = sizeof(real) == 4 ? 4 : 2;
+};
+
+// w[d] for a run-time d in 0..3 without indexing a local array.
+template <typename real>
+__device__ __forceinline__ real pick4(const real w[4], int d) {
+  return d == 0 ? w[0] : d == 1 ? w[1] : d == 2 ? w[2] : w[3];
+}
+
+// K4a: spreading, first pass (Eq. 13). One warp per source tile S: its bucket is sorted by
+// vertex index (rank by comparison, at most 64 entries), the vertices' stencil records and
+// forces (completed with the volume term -kV (V - V0)/V0 dV/dq) are staged in shared memory,
+// and the vertices are then added one after another into the 7x7x7 region of S, each lane
+// adding two of the 64 stencil nodes of a vertex (distinct nodes, so no atomics). The region
+// is written out and its index pushed to the (up to 8) tiles T = S + {0,1}^3 it overlaps.
+// Vertices in the overflow list (more than 64 in a tile) follow in list order. The order of
+// summation is fixed by the sorted buckets.
+template <typename real>
+__global__ void __launch_bounds__(32 * SrcWarps<real>::value) spread_source_kernel(
+    const int *__restrict__ tile_slot, const int *__restrict__ slot_tile,
+    const int *__restrict__ nslots_ptr, const int *__restrict__ slot_count,
+    const int *__restrict__ src_index, const int *__restrict__ bucket,
+    const int *__restrict__ overflow, const int *__restrict__ ovf_count_ptr,
+    const StencilRec<real> *__restrict__ stencil, const Vec4<real> *__restrict__ phi,
+    const Vec4<real> *__restrict__ gvol, const double *__restrict__ vol_partial, VolumeParams vp,
+    int *__restrict__ health, Vec4<real> *__restrict__ Rslot, int *__restrict__ out_src, Dims D) {
+  constexpr int W = SrcWarps<real>::value;
+  __shared__ Vec4<real> s_region[W][REGION_NODES];
+  __shared__ real s_w[W][BUCKET_CAP][12];
+  __shared__ Vec4<real> s_f[W][BUCKET_CAP];
+  __shared__ int s_b[W][BUCKET_CAP][3];
+  const int nslots = min(*nslots_ptr, D.max_slots);
+  const int novf = *ovf_count_ptr;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  double V;
+  const real coef = (real)volume_coef(vol_partial, vp.vol_blocks, vp.V0, vp.kV, vp.volume_on, &V);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !(fabs(V / vp.V0 - 1.0) <= 0.05))
+    atomicOr(health, H_VOLUME);
+  Vec4<real> *region = s_region[wq];
+  // the two stencil nodes of this lane
+  const int dxa = lane & 3, dya = (lane >> 2) & 3, dza = lane >> 4;  // node lane; node lane + 32
+  for (int s = blockIdx.x * W + wq; s < nslots; s += gridDim.x * W) {
+    const int cnt = slot_count[s];
+    if (cnt == 0) continue;  // no vertex has its base node here: no region
+    const int n = min(cnt, BUCKET_CAP);
+    const int nspill = cnt > BUCKET_CAP ? novf : 0;  // scan the overflow list only if it spilled
+    const int t = slot_tile[s];
+    const int tsx = t % D.ntx, tsy = (t / D.ntx) % D.nty, tsz = t / (D.ntx * D.nty);
+    const int Sx = tsx * TILE, Sy = tsy * TILE, Sz = tsz * TILE;
+    const int reg = src_index[s];
+    // push the region to the tiles it overlaps: T = S + e, seen from T as source e
+    if (lane < 8) {
+      int ux = tsx + (lane & 1), uy = tsy + ((lane >> 1) & 1), uz = tsz + (lane >> 2);
+      ux = ux >= D.ntx ? ux - D.ntx : ux;
+      uy = uy >= D.nty ? uy - D.nty : uy;
+      bool ok = true;
+      if (uz >= D.ntz) {
+        if (D.has_walls) ok = false;
+        uz -= D.ntz;
+      }
+      if (ok) {
+        const int slot_t = tile_slot[(uz * D.nty + uy) * D.ntx + ux];
+        if (slot_t >= 0) out_src[8 * (size_t)slot_t + lane] = reg;
+      }
+    }
+    // sort the bucket by vertex index and stage the records in that order
+    const int *bk = bucket + (size_t)s * BUCKET_CAP;
     const int v0 = lane < n ? bk[lane] : 0x7fffffff;
     const int v1 = lane + 32 < n ? bk[lane + 32] : 0x7fffffff;
     int r0 = 0, r1 = 0;
@@ -293,221 +365,116 @@ __global__ void __launch_bounds__(256) sort_buckets_kernel(const int *__restrict
       r0 += vm < v0;
       r1 += vm < v1;
     }
+    for (int h = 0; h < 2; h++) {
+      const int v = h ? v1 : v0;
+      const int r = h ? r1 : r0;
+      if ((h ? lane + 32 : lane) >= n) continue;
+      const StencilRec<real> rec = stencil[v];
+      const Vec4<real> pv = phi[v], gv = gvol[v];
+      for (int k = 0; k < 4; k++) {
+        s_w[wq][r][k] = rec.w[0][k];
+        s_w[wq][r][4 + k] = rec.w[1][k];
+        s_w[wq][r][8 + k] = rec.w[2][k];
+      }
+      s_f[wq][r] = Vec4<real>{pv.x - coef * gv.x, pv.y - coef * gv.y, pv.z - coef * gv.z, real(0)};
+      // base relative to S_lo (x, y wrapped into [0, n) by the vertex kernel)
+      s_b[wq][r][0] = rec.base[0] - Sx;
+      s_b[wq][r][1] = rec.base[1] - Sy;
+      s_b[wq][r][2] = rec.base[2] - Sz;
+    }
+    for (int k = lane; k < REGION_NODES; k += 32) region[k] = Vec4<real>{0, 0, 0, 0};
     __syncwarp();
-    if (lane < n) bk[r0] = v0;
-    if (lane + 32 < n) bk[r1] = v1;
+    for (int c = 0; c < n; c++) {
+      const int bx = s_b[wq][c][0], by = s_b[wq][c][1], bz = s_b[wq][c][2];
+      const Vec4<real> f = s_f[wq][c];
+      const real wxy = s_w[wq][c][dxa] * s_w[wq][c][4 + dya];
+      for (int h = 0; h < 2; h++) {
+        const int dz = dza + 2 * h;  // node lane + 32 h has the same dx, dy and dz + 2
+        const int rz = bz + dz;
+        if (rz < 0 || rz >= REGION) continue;  // beyond the lattice in z
+        const real w = wxy * s_w[wq][c][8 + dz];
+        Vec4<real> &o = region[(rz * REGION + by + dya) * REGION + bx + dxa];
+        o.x += w * f.x;
+        o.y += w * f.y;
+        o.z += w * f.z;
+      }
+      __syncwarp();
+    }
+    for (int c = 0; c < nspill; c++) {  // vertices spilled from this tile's bucket
+      const int v = overflow[c];
+      const StencilRec<real> rec = stencil[v];
+      const int bzc = min(max(rec.base[2], 0), D.nz - 1);
+      const int bx = rec.base[0] - Sx, by = rec.base[1] - Sy, bz = rec.base[2] - Sz;
+      if (bx < 0 || bx > 3 || by < 0 || by > 3 || (bzc >> 2) * TILE != Sz) continue;
+      const Vec4<real> pv = phi[v], gv = gvol[v];
+      const real fx = pv.x - coef * gv.x, fy = pv.y - coef * gv.y, fz = pv.z - coef * gv.z;
+      const real wxy = pick4(rec.w[0], dxa) * pick4(rec.w[1], dya);
+      for (int h = 0; h < 2; h++) {
+        const int dz = dza + 2 * h;
+        const int rz = bz + dz;
+        if (rz < 0 || rz >= REGION) continue;
+        const real w = wxy * pick4(rec.w[2], dz);
+        Vec4<real> &o = region[(rz * REGION + by + dya) * REGION + bx + dxa];
+        o.x += w * fx;
+        o.y += w * fy;
+        o.z += w * fz;
+      }
+      __syncwarp();
+    }
+    Vec4<real> *out = Rslot + (size_t)reg * REGION_NODES;
+    for (int k = lane; k < REGION_NODES; k += 32) out[k] = region[k];
+    __syncwarp();
   }
 }
 
-// Candidates staged per tile and pass of the spreading kernel (shared memory: 4 tiles x chunk
-// x 16 values: 16 KB in float, 32 KB in double).
+// K4b: spreading, second pass. One 64-thread block per active tile T (grid-stride), thread =
+// node (lx, ly, lz): the force is the sum, in the fixed order e = 0..7, of the regions of the
+// source tiles S = T - e pushed by K4a; the node sits at (l + 4 e) in S's region. On a
+// periodic axis only 4 nodes long S - e and S coincide and the two terms are the node's two
+// images in the region. Force landing on a wall layer is dropped.
 template <typename real>
-struct SpreadChunk {
-  static constexpr int value = 64;
-};
-
-// w[d] for a run-time d in 0..3 without indexing a local array.
-template <typename real>
-__device__ __forceinline__ real pick4(const real w[4], int d) {
-  return d == 0 ? w[0] : d == 1 ? w[1] : d == 2 ? w[2] : w[3];
-}
-// Active tiles per 64-thread spreading block (16 threads per tile).
-constexpr int SPREAD_TILES = 4;
-
-struct VolumeParams {
-  double V0, kV;
-  int volume_on, vol_blocks;
-};
-
-// K4b: spreading (Eq. 13). A 64-thread block handles 4 active tiles; 16 threads per tile,
-// thread (ly, lz) owns the x-row of 4 nodes (0..3, ly, lz). The candidates of a tile are the
-// vertices binned in its eight source tiles T - {0,1}^3 (every vertex whose stencil reaches
-// T lies there), in bucket order, then the overflow list. When a candidate is staged its
-// nodal force is completed with the volume term and its one-dimensional weights are
-// re-indexed to the tile's node coordinates, zero where the stencil misses the tile, so the
-// inner loop is a branch-free separable product. Each thread writes its own nodes once: no
-// atomics, and the summation order is fixed by the sorted buckets (the overflow list,
-// normally empty, follows arrival order).
-template <typename real>
-__global__ void __launch_bounds__(64) spread_kernel(
-    const int *__restrict__ tile_slot, const int *__restrict__ slot_tile,
-    const int *__restrict__ nslots_ptr, const int *__restrict__ slot_count,
-    const int *__restrict__ bucket, const int *__restrict__ overflow,
-    const int *__restrict__ ovf_count_ptr, const StencilRec<real> *__restrict__ stencil,
-    const Vec4<real> *__restrict__ phi, const Vec4<real> *__restrict__ gvol,
-    const double *__restrict__ vol_partial, VolumeParams vp, int *__restrict__ health,
+__global__ void __launch_bounds__(64) spread_gather_kernel(
+    const int *__restrict__ slot_tile, const int *__restrict__ nslots_ptr,
+    const int *__restrict__ out_src, const Vec4<real> *__restrict__ Rslot,
     Vec4<real> *__restrict__ Fslot, Dims D) {
-  constexpr int SPREAD_CHUNK = SpreadChunk<real>::value;
-  __shared__ int s_src_slot[SPREAD_TILES][8];
-  __shared__ int s_src_start[SPREAD_TILES][9];
-  __shared__ Vec4<real> s_wx[SPREAD_TILES][SPREAD_CHUNK];
-  __shared__ real s_wy[SPREAD_TILES][SPREAD_CHUNK][4];
-  __shared__ real s_wz[SPREAD_TILES][SPREAD_CHUNK][4];
-  __shared__ Vec4<real> s_phi[SPREAD_TILES][SPREAD_CHUNK];
-  __shared__ double s_coef;
-  __shared__ int s_passes[2];
   const int nslots = min(*nslots_ptr, D.max_slots);
-  const int novf = *ovf_count_ptr;
-  if (threadIdx.x < 32) {
-    double V;
-    const double coef = volume_coef(vol_partial, vp.vol_blocks, vp.V0, vp.kV, vp.volume_on, &V);
-    if (threadIdx.x == 0) {
-      s_coef = coef;
-      if (blockIdx.x == 0 && !(fabs(V / vp.V0 - 1.0) <= 0.05)) atomicOr(health, H_VOLUME);
+  const int tid = threadIdx.x;
+  const int lx = tid & 3, ly = (tid >> 2) & 3, lz = tid >> 4;
+  for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
+    const int *src = out_src + 8 * (size_t)b;
+    real f[3] = {0, 0, 0};
+    for (int e = 0; e < 8; e++) {
+      const int reg = src[e];
+      const int rx = lx + 4 * (e & 1), ry = ly + 4 * ((e >> 1) & 1), rz = lz + 4 * (e >> 2);
+      if (reg < 0 || rx >= REGION || ry >= REGION || rz >= REGION) continue;
+      const Vec4<real> r = Rslot[(size_t)reg * REGION_NODES + (rz * REGION + ry) * REGION + rx];
+      f[0] += r.x;
+      f[1] += r.y;
+      f[2] += r.z;
     }
-  }
-  const int tq = threadIdx.x >> 4;  // tile of this thread within the block
-  const int r = threadIdx.x & 15;
-  const int ly = r & 3, lz = r >> 2;
-  for (int b0 = blockIdx.x * SPREAD_TILES; b0 < nslots; b0 += gridDim.x * SPREAD_TILES) {
-    const int b = b0 + tq;
-    const bool active = b < nslots;
-    int tx = 0, ty = 0, tz = 0;
-    if (active) {
-      const int t = slot_tile[b];
-      tx = t % D.ntx;
-      ty = (t / D.ntx) % D.nty;
-      tz = t / (D.ntx * D.nty);
-    }
-    __syncthreads();  // shared arrays of the previous round are no longer read
-    if (r < 8) {
-      int slot = -1, count = 0;
-      if (active) {
-        int sx = tx - (r & 1), sy = ty - ((r >> 1) & 1), sz = tz - (r >> 2);
-        sx = sx < 0 ? sx + D.ntx : sx;
-        sy = sy < 0 ? sy + D.nty : sy;
-        bool ok = true;
-        if (sz < 0) {
-          if (D.has_walls) ok = false;
-          sz += D.ntz;
-        }
-        // with a single tile along an axis both offsets name the same tile
-        if (((r & 1) && D.ntx == 1) || (((r >> 1) & 1) && D.nty == 1) || ((r >> 2) && D.ntz == 1))
-          ok = false;
-        if (ok) {
-          slot = tile_slot[(sz * D.nty + sy) * D.ntx + sx];
-          if (slot >= 0) count = min(slot_count[slot], BUCKET_CAP);
-          else slot = -1;
-        }
-      }
-      s_src_slot[tq][r] = slot;
-      s_src_start[tq][r + 1] = count;
-    }
-    __syncthreads();
-    if (r == 0) {
-      s_src_start[tq][0] = 0;
-      for (int k = 1; k <= 8; k++) s_src_start[tq][k] += s_src_start[tq][k - 1];
-    }
-    __syncthreads();
-    const real coef = (real)s_coef;
-    const int nb = s_src_start[tq][8];
-    const int total = active ? nb + novf : 0;
-    // the block runs as many passes as its largest tile needs
-    int passes = (total + SPREAD_CHUNK - 1) / SPREAD_CHUNK;
-    passes = max(passes, __shfl_xor_sync(0xffffffffu, passes, 16));
-    if ((threadIdx.x & 31) == 0) s_passes[threadIdx.x >> 5] = passes;
-    __syncthreads();
-    passes = max(s_passes[0], s_passes[1]);
-    const int X0 = tx * TILE, Y0 = ty * TILE, Z0 = tz * TILE;
-    real acc[4][3];
-    for (int i = 0; i < 4; i++) acc[i][0] = acc[i][1] = acc[i][2] = 0;
-    for (int p = 0; p < passes; p++) {
-      const int c0 = p * SPREAD_CHUNK;
-      const int nload = max(0, min(SPREAD_CHUNK, total - c0));
-      if (p > 0) __syncthreads();
-      // Stage the candidates whose stencil overlaps the tile, keeping their order: lanes of a
-      // tile take 16 candidates per round and a ballot compacts the ones that overlap.
-      const int lane = threadIdx.x & 31;
-      const int wmax = max(nload, __shfl_xor_sync(0xffffffffu, nload, 16));
-      int nkeep = 0;
-      for (int k0 = 0; k0 < wmax; k0 += 16) {
-        const int k = k0 + r;
-        bool keep = false;
-        real wx[4], wy[4], wz[4];
-        Vec4<real> ph;
-        if (k < nload) {
-          const int g = c0 + k;
-          int v;
-          if (g < nb) {
-            int src = 0;
-            while (g >= s_src_start[tq][src + 1]) src++;
-            v = bucket[(size_t)s_src_slot[tq][src] * BUCKET_CAP + (g - s_src_start[tq][src])];
-          } else {
-            v = overflow[g - nb];
-          }
-          const StencilRec<real> rec = stencil[v];
-          real sx = 0, sy = 0, sz = 0;
-          for (int l = 0; l < 4; l++) {
-            int dx = X0 + l - rec.base[0];
-            dx = dx < 0 ? dx + D.nx : dx;
-            int dy = Y0 + l - rec.base[1];
-            dy = dy < 0 ? dy + D.ny : dy;
-            int dz = Z0 + l - rec.base[2];
-            if (!D.has_walls) dz = dz < 0 ? dz + D.nz : dz;
-            wx[l] = dx < 4 ? pick4(rec.w[0], dx) : real(0);
-            wy[l] = dy < 4 ? pick4(rec.w[1], dy) : real(0);
-            wz[l] = (unsigned)dz < 4u ? pick4(rec.w[2], dz) : real(0);
-            sx += wx[l];
-            sy += wy[l];
-            sz += wz[l];
-          }
-          keep = sx > real(0) && sy > real(0) && sz > real(0);
-          if (keep) {
-            const Vec4<real> pv = phi[v], gv = gvol[v];
-            ph = Vec4<real>{pv.x - coef * gv.x, pv.y - coef * gv.y, pv.z - coef * gv.z, real(0)};
-          }
-        }
-        const unsigned mine = (__ballot_sync(0xffffffffu, keep) >> (lane & 16)) & 0xffffu;
-        if (keep) {
-          const int pos = nkeep + __popc(mine & ((1u << r) - 1u));
-          s_wx[tq][pos] = Vec4<real>{wx[0], wx[1], wx[2], wx[3]};
-          for (int l = 0; l < 4; l++) {
-            s_wy[tq][pos][l] = wy[l];
-            s_wz[tq][pos][l] = wz[l];
-          }
-          s_phi[tq][pos] = ph;
-        }
-        nkeep += __popc(mine);
-      }
-      __syncthreads();
-      for (int k = 0; k < nkeep; k++) {
-        const real t = s_wy[tq][k][ly] * s_wz[tq][k][lz];
-        const Vec4<real> ph = s_phi[tq][k];
-        const Vec4<real> wxv = s_wx[tq][k];
-        const real g0 = t * ph.x, g1 = t * ph.y, g2 = t * ph.z;
-        acc[0][0] += wxv.x * g0; acc[0][1] += wxv.x * g1; acc[0][2] += wxv.x * g2;
-        acc[1][0] += wxv.y * g0; acc[1][1] += wxv.y * g1; acc[1][2] += wxv.y * g2;
-        acc[2][0] += wxv.z * g0; acc[2][1] += wxv.z * g1; acc[2][2] += wxv.z * g2;
-        acc[3][0] += wxv.w * g0; acc[3][1] += wxv.w * g1; acc[3][2] += wxv.w * g2;
-      }
-    }
-    if (active) {
-      // force landing on a wall layer is dropped
-      const int Z = Z0 + lz;
-      const bool drop = D.has_walls && (Z == 0 || Z >= D.nz - 1);
-      Vec4<real> *Fs = Fslot + (size_t)b * TILE_CELLS + 4 * ly + 16 * lz;
-      for (int l = 0; l < 4; l++) {
-        Vec4<real> o;
-        o.x = drop ? real(0) : acc[l][0];
-        o.y = drop ? real(0) : acc[l][1];
-        o.z = drop ? real(0) : acc[l][2];
-        o.w = real(0);
-        Fs[l] = o;
-      }
-    }
+    const int Z = (slot_tile[b] / (D.ntx * D.nty)) * TILE + lz;
+    const bool drop = D.has_walls && (Z == 0 || Z >= D.nz - 1);
+    Vec4<real> o;
+    o.x = drop ? real(0) : f[0];
+    o.y = drop ? real(0) : f[1];
+    o.z = drop ? real(0) : f[2];
+    o.w = real(0);
+    Fslot[(size_t)b * TILE_CELLS + tid] = o;
   }
 }
 
 // Claim tile t in map (tile_slot, slot_tile, nslots): the first claimant takes a new slot.
 // A plain read first keeps the many vertices of an already-claimed tile off the atomic.
 __device__ __forceinline__ void claim_tile(int t, int *tile_slot, int *slot_tile, int *nslots,
-                                           int *slot_count, int *health, int max_slots) {
+                                           int *slot_count, int *out_src, int *health,
+                                           int max_slots) {
   if (*(volatile int *)&tile_slot[t] != -1) return;
   if (atomicCAS(&tile_slot[t], -1, -2) == -1) {
     const int s = atomicAdd(nslots, 1);
     if (s < max_slots) {
       slot_tile[s] = t;
       slot_count[s] = 0;
+      for (int e = 0; e < 8; e++) out_src[8 * (size_t)s + e] = -1;
       atomicExch(&tile_slot[t], s);
     } else {
       atomicOr(health, H_CAPACITY);
@@ -548,7 +515,7 @@ __device__ __forceinline__ AxisTiles axis_tiles(double p, int nt, double inv_n, 
 // axis k) of the stencil described by ax.
 __device__ __forceinline__ void mark_tile(const AxisTiles ax[3], int e, const Dims &D,
                                           int *tile_slot, int *slot_tile, int *nslots,
-                                          int *slot_count, int *health) {
+                                          int *slot_count, int *out_src, int *health) {
   int t[3];
   for (int k = 0; k < 3; k++) {
     const bool up = (e >> k) & 1;
@@ -556,7 +523,7 @@ __device__ __forceinline__ void mark_tile(const AxisTiles ax[3], int e, const Di
     t[k] = up ? ax[k].t1 : ax[k].t0;
   }
   claim_tile((t[2] * D.nty + t[1]) * D.ntx + t[0], tile_slot, slot_tile, nslots, slot_count,
-             health, D.max_slots);
+             out_src, health, D.max_slots);
 }
 
 // K2: interpolation (Eq. 11) and the Euler update (Eq. 12); 4 lanes per vertex, lane dz
@@ -570,7 +537,7 @@ __global__ void __launch_bounds__(256) interp_kernel(
     const double *__restrict__ xref, Vec4<real> *__restrict__ disp,
     double3 ub, double3 ut, Dims D, int *__restrict__ next_tile_slot,
     int *__restrict__ next_slot_tile, int *__restrict__ next_nslots, int *__restrict__ slot_count,
-    int *__restrict__ health) {
+    int *__restrict__ out_src, int *__restrict__ health) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = gid >> 2;
   const int dz = gid & 3;
@@ -654,8 +621,10 @@ __global__ void __launch_bounds__(256) interp_kernel(
       ax[0] = axis_tiles(pn[0], D.ntx, D.inx, true);
       ax[1] = axis_tiles(pn[1], D.nty, D.iny, true);
       ax[2] = axis_tiles(pn[2], D.ntz, D.inz, !D.has_walls);
-      mark_tile(ax, dz, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, health);
-      mark_tile(ax, dz + 4, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, health);
+      mark_tile(ax, dz, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, out_src,
+                health);
+      mark_tile(ax, dz + 4, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, out_src,
+                health);
     }
   }
 }
@@ -665,7 +634,8 @@ __global__ void __launch_bounds__(256) interp_kernel(
 template <typename real>
 __global__ void mark_kernel(int nv, const double *__restrict__ q, const double *__restrict__ xref,
                             Vec4<real> *__restrict__ disp, Dims D, int *tile_slot,
-                            int *slot_tile, int *nslots, int *slot_count, int *health) {
+                            int *slot_tile, int *nslots, int *slot_count, int *out_src,
+                            int *health) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = gid >> 3, e = gid & 7;
   if (v >= nv) return;
@@ -683,7 +653,7 @@ __global__ void mark_kernel(int nv, const double *__restrict__ q, const double *
     ax[0] = axis_tiles(p[0], D.ntx, D.inx, true);
     ax[1] = axis_tiles(p[1], D.nty, D.iny, true);
     ax[2] = axis_tiles(p[2], D.ntz, D.inz, !D.has_walls);
-    mark_tile(ax, e, D, tile_slot, slot_tile, nslots, slot_count, health);
+    mark_tile(ax, e, D, tile_slot, slot_tile, nslots, slot_count, out_src, health);
   }
 }
 
@@ -692,7 +662,10 @@ __global__ void clear_counts_kernel(const int *__restrict__ nslots, int *__restr
   const int n = min(*nslots, max_slots);
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
     slot_count[s] = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *ovf_count = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ovf_count[0] = 0;
+    ovf_count[2] = 0;
+  }
 }
 
 template <typename real>
@@ -774,26 +747,29 @@ cudaError_t vertex_forces_t(Ctx &c, int bin, cudaStream_t st) {
   vertex_kernel<real><<<(c.nv + 255) / 256, 256, 0, st>>>(
       c.nv, c.vf_start, c.vf_list, (const real *)c.fcontrib, (const real *)c.fnorm, c.q,
       (Vec4<real> *)c.phi, (Vec4<real> *)c.gvol, (StencilRec<real> *)c.stencil, bin, c.tile_slot[c.map],
-      c.slot_count, c.bucket, c.overflow, c.counters + 2, c.counters + 3,
-      bin == 2 ? c.counters + (c.map ^ 1) : nullptr, dims_of(c));
+      c.slot_count, c.bucket, c.overflow, c.counters + 2, c.src_index, c.counters + 4,
+      c.counters + 3, bin == 2 ? c.counters + (c.map ^ 1) : nullptr, dims_of(c));
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t spread_t(Ctx &c, cudaStream_t st) {
-  int sgrid = c.sm_count * 8;
-  if (sgrid * 8 > c.max_slots) sgrid = (c.max_slots + 7) / 8;
-  sort_buckets_kernel<<<sgrid, 256, 0, st>>>(c.counters + c.map, c.slot_count, c.bucket, c.max_slots);
+  // persistent grids sized to the SMs the interface chain runs on
+  constexpr int W = SrcWarps<real>::value;
+  const int sms = c.ib_sms > 0 ? c.ib_sms : c.sm_count;
+  int g1 = sms * 8;
+  if (g1 * W > c.max_slots) g1 = (c.max_slots + W - 1) / W;
+  spread_source_kernel<real><<<g1 < 1 ? 1 : g1, 32 * W, 0, st>>>(
+      c.tile_slot[c.map], c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.src_index,
+      c.bucket, c.overflow, c.counters + 2, (const StencilRec<real> *)c.stencil,
+      (const Vec4<real> *)c.phi, (const Vec4<real> *)c.gvol, c.vol_partial, volume_params(c),
+      c.counters + 3, (Vec4<real> *)c.Rslot, c.out_src[c.map], dims_of(c));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // persistent grid: enough resident blocks for the SMs the interface chain runs on
-  int grid = (c.ib_sms > 0 ? c.ib_sms : c.sm_count) * 12;
-  if (grid * SPREAD_TILES > c.max_slots) grid = (c.max_slots + SPREAD_TILES - 1) / SPREAD_TILES;
-  if (grid < 1) grid = 1;
-  spread_kernel<real><<<grid, TILE_CELLS, 0, st>>>(
-      c.tile_slot[c.map], c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.bucket,
-      c.overflow, c.counters + 2, (const StencilRec<real> *)c.stencil, (const Vec4<real> *)c.phi,
-      (const Vec4<real> *)c.gvol, c.vol_partial, volume_params(c), c.counters + 3,
+  int g2 = sms * 16;
+  if (g2 > c.max_slots) g2 = c.max_slots;
+  spread_gather_kernel<real><<<g2 < 1 ? 1 : g2, TILE_CELLS, 0, st>>>(
+      c.slot_tile[c.map], c.counters + c.map, c.out_src[c.map], (const Vec4<real> *)c.Rslot,
       (Vec4<real> *)c.Fslot[c.map], dims_of(c));
   return cudaGetLastError();
 }
@@ -806,7 +782,7 @@ cudaError_t interp_t(Ctx &c, cudaStream_t st) {
       c.nv, (const StencilRec<real> *)c.stencil, c.tile_slot[c.map], (const Vec4<real> *)c.Uslot,
       c.q, c.qdot, c.xref, (Vec4<real> *)c.disp, make_double3(c.ub[0], c.ub[1], c.ub[2]),
       make_double3(c.ut[0], c.ut[1], c.ut[2]), dims_of(c), c.tile_slot[other],
-      c.slot_tile[other], c.counters + other, c.slot_count, c.counters + 3);
+      c.slot_tile[other], c.counters + other, c.slot_count, c.out_src[other], c.counters + 3);
   return cudaGetLastError();
 }
 
@@ -842,11 +818,11 @@ cudaError_t launch_mark(Ctx &c) {
   if (c.precision == IBLB_FP64)
     mark_kernel<double><<<blocks, 256, 0, c.stream>>>(
         c.nv, c.q, c.xref, (Vec4<double> *)c.disp, dims_of(c), c.tile_slot[c.map],
-        c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.counters + 3);
+        c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.out_src[c.map], c.counters + 3);
   else
     mark_kernel<float><<<blocks, 256, 0, c.stream>>>(
         c.nv, c.q, c.xref, (Vec4<float> *)c.disp, dims_of(c), c.tile_slot[c.map],
-        c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.counters + 3);
+        c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.out_src[c.map], c.counters + 3);
   return cudaGetLastError();
 }
 

@@ -84,7 +84,11 @@ struct Ctx {
   int max_slots = 0;
   int *tile_slot[2] = {nullptr, nullptr};  // [ntiles] slot or -1
   int *slot_tile[2] = {nullptr, nullptr};  // [max_slots] tile id of each active slot
-  int *counters = nullptr;                 // [0..1] nslots per map, [2] overflow count, [3] health
+  int *counters = nullptr;  // [0..1] nslots per map, [2] overflow count, [3] health, [4] sources
+  int *src_index = nullptr;                // [max_slots] region of a source tile (slot)
+  void *Rslot = nullptr;                   // [max_sources][343] Vec4 spreading regions
+  int *out_src[2] = {nullptr, nullptr};    // per map: [max_slots][8] region of source T - e
+  int max_sources = 0;
   int *slot_count = nullptr;               // [max_slots] vertices in each source bucket
   int *bucket = nullptr;                   // [max_slots][BUCKET_CAP]
   int *overflow = nullptr;                 // [nv] vertices not fitting in their bucket
