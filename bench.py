@@ -39,6 +39,8 @@ def workload(name: str):
         return inputs.shear_256_fp32()
     if name == "wetting128":
         return inputs.wetting_128x128x96()
+    if name == "box128":
+        return inputs.shear_256_fp32_box(128)
     if name == "shear32":
         return inputs.shear_32_fp64()
     raise SystemExit(f"unknown workload {name}")
@@ -167,11 +169,39 @@ def run_reference(args, wl, rank):
 
 def config_of(wl):
     v, f = wl.mesh()
+    arr_gb = 19 * wl.cells * (8 if wl.precision == "fp64" else 4) / 1e9
     return {"workload": wl.name, "lattice": [wl.nx, wl.ny, wl.nz], "nodes": wl.cells,
             "vertices": int(v.shape[0]), "faces": int(f.shape[0]), "tau": wl.tau,
             "wall_u": [wl.wall_u_bottom[0], wl.wall_u_top[0]],
             "alpha": list(wl.alpha), "precision": wl.precision,
-            "l2": "no flush: the two population arrays (2 x 1.27 GB) exceed the 129 MB L2"}
+            "l2": f"no flush: the two population arrays (2 x {arr_gb:.2f} GB) exceed the 129 MB L2"}
+
+
+def k1_source_hash():
+    """Hash of the stream-collide kernel's sources: DRAM counters taken on another build of
+    the kernel do not describe this one."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("lattice_kernels.cu", "iblb_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2305_18919_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def k1_traffic_per_node():
+    """DRAM bytes (read + write) per fluid node of one stream-collide launch, from the committed
+    ncu summary, if it was taken on the current kernel source; else None."""
+    import re
+    path = os.path.join(ROOT, "profiles", "stream_collide_kernel_box128.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic per fluid node: ([0-9.]+) B", text)
+    hsh = re.search(r"kernel source sha256: ([0-9a-f]{64})", text)
+    if not m or not hsh or hsh.group(1) != k1_source_hash():
+        return None
+    return float(m.group(1))
 
 
 def run_gpu(args, wl, rank, world):
@@ -244,18 +274,14 @@ def run_gpu(args, wl, rank, world):
     achieved = bpc * fluid / (k1_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "stream_collide_kernel<float,false>",
+                "kernel": "stream_collide_kernel<float,false,false>",
                 "algorithmic_bytes_per_launch": bpc * fluid,
                 "k1_ms_avg": round(k1_avg_ms, 5), "peak_source": peak_note,
                 "step_frac": round(bpc * fluid / (ms_step * 1e-3) / 1e9 / peak, 4)}
-    traffic = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
-    if os.path.exists(traffic):
-        try:
-            tr = json.load(open(traffic))
-            if tr.get("workload") == wl.name and tr.get("bytes_per_launch"):
-                roofline["traffic"] = tr["bytes_per_launch"]
-        except Exception:
-            pass
+    per_node = k1_traffic_per_node()
+    if per_node is not None:
+        # measured on the 128^3 profiling case, scaled to this launch by its fluid nodes
+        roofline["traffic"] = int(round(per_node * fluid))
     clocks = clk.summary()
     ib_sms = lat.interface_sms()
     lat.close()
@@ -284,8 +310,8 @@ def run_gpu(args, wl, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="shear256")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

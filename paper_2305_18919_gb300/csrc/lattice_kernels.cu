@@ -165,14 +165,6 @@ __device__ __forceinline__ void collide(real f[Q], const real F[3], const LatPar
   }
 }
 
-template <typename real, bool FORCE>
-__device__ __forceinline__ void collide_store(real f[Q], const real F[3], real *__restrict__ fout,
-                                              size_t n, const LatParams<real> &P) {
-  collide<real, FORCE>(f, F, P);
-#pragma unroll
-  for (int i = 0; i < Q; i++) fout[(size_t)i * P.ncell + n] = f[i];
-}
-
 template <typename real>
 struct Vec2;
 template <>
@@ -184,23 +176,17 @@ struct Vec2<double> {
   using T = double2;
 };
 
-// K1: fused stream-collide of every fluid node with the uniform body force only (FORCE: the
-// body force is non-zero). The nodes of active interface tiles are collided again by K1t with
-// their interface force, so this pass does not wait for the interface chain of the step.
-// Each thread owns the two nodes (x0, x0 + 1), x0 even: populations that do not move along x
-// and every store are one aligned 2-wide access, and the address arithmetic is shared.
-template <typename real, bool FIRST, bool FORCE>
-__global__ void __launch_bounds__(128) stream_collide_kernel(const real *__restrict__ fin,
-                                                             real *__restrict__ fout,
-                                                             const LatParams<real> P, int z0) {
+// Post-streaming populations a (node x0) and b (node x0 + 1) of two fluid nodes, x0 even,
+// from post-collision array `fin` (FIRST: `fin` already holds post-streaming populations,
+// read in place). Populations that do not move along x are one aligned 2-wide load; a link
+// whose source is a wall node is bounced back (opposite population of the same node plus the
+// moving-wall term).
+template <typename real, bool FIRST>
+__device__ __forceinline__ void load_pair(const real *__restrict__ fin, const LatParams<real> &P,
+                                          int x0, int y, int z, real a[Q], real b[Q]) {
   using V2 = typename Vec2<real>::T;
-  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y;
-  const int z = blockIdx.z + z0;
-  if (x0 >= P.nx) return;
   const size_t plane = (size_t)P.nx * P.ny;
   const size_t n = (size_t)z * plane + (size_t)y * P.nx + x0;
-  real a[Q], b[Q];  // populations of nodes x0 and x0 + 1
   if (FIRST) {
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -208,46 +194,48 @@ __global__ void __launch_bounds__(128) stream_collide_kernel(const real *__restr
       a[i] = v.x;
       b[i] = v.y;
     }
-  } else {
-    const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;       // source of node x0 for c_x = +1
-    const int xp = x0 + 2 == P.nx ? 0 : x0 + 2;       // source of node x0 + 1 for c_x = -1
-    const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
-    int zm = z - 1, zp = z + 1;
-    if (!P.has_walls) {
-      zm = z == 0 ? P.nz - 1 : zm;
-      zp = z == P.nz - 1 ? 0 : zp;
-    }
-    const bool wall_below = P.has_walls && zm == 0;
-    const bool wall_above = P.has_walls && zp == P.nz - 1;
-    const size_t zo[3] = {(size_t)zm * plane, (size_t)z * plane, (size_t)zp * plane};
-    const size_t yo[3] = {(size_t)ym * P.nx, (size_t)y * P.nx, (size_t)yp * P.nx};
+    return;
+  }
+  const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;   // source of node x0 for c_x = +1
+  const int xp = x0 + 2 == P.nx ? 0 : x0 + 2;   // source of node x0 + 1 for c_x = -1
+  const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
+  int zm = z - 1, zp = z + 1;
+  if (!P.has_walls) {
+    zm = z == 0 ? P.nz - 1 : zm;
+    zp = z == P.nz - 1 ? 0 : zp;
+  }
+  const bool wall_below = P.has_walls && zm == 0;
+  const bool wall_above = P.has_walls && zp == P.nz - 1;
+  const size_t zo[3] = {(size_t)zm * plane, (size_t)z * plane, (size_t)zp * plane};
+  const size_t yo[3] = {(size_t)ym * P.nx, (size_t)y * P.nx, (size_t)yp * P.nx};
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-      if ((cz(i) > 0 && wall_below) || (cz(i) < 0 && wall_above)) {
-        // half-way bounce-back: opposite post-collision population of the same nodes
-        const V2 v = *reinterpret_cast<const V2 *>(fin + (size_t)opp(i) * P.ncell + n);
-        const real wall = cz(i) > 0 ? P.wb[i] : P.wt[i];
-        a[i] = v.x + wall;
-        b[i] = v.y + wall;
-        continue;
-      }
-      const real *row = fin + (size_t)i * P.ncell + zo[1 - cz(i)] + yo[1 - cy(i)];
-      if (cx(i) == 0) {
-        const V2 v = *reinterpret_cast<const V2 *>(row + x0);
-        a[i] = v.x;
-        b[i] = v.y;
-      } else if (cx(i) > 0) {
-        a[i] = row[xm];
-        b[i] = row[x0];
-      } else {
-        a[i] = row[x0 + 1];
-        b[i] = row[xp];
-      }
+  for (int i = 0; i < Q; i++) {
+    if ((cz(i) > 0 && wall_below) || (cz(i) < 0 && wall_above)) {
+      const V2 v = *reinterpret_cast<const V2 *>(fin + (size_t)opp(i) * P.ncell + n);
+      const real wall = cz(i) > 0 ? P.wb[i] : P.wt[i];
+      a[i] = v.x + wall;
+      b[i] = v.y + wall;
+      continue;
+    }
+    const real *row = fin + (size_t)i * P.ncell + zo[1 - cz(i)] + yo[1 - cy(i)];
+    if (cx(i) == 0) {
+      const V2 v = *reinterpret_cast<const V2 *>(row + x0);
+      a[i] = v.x;
+      b[i] = v.y;
+    } else if (cx(i) > 0) {
+      a[i] = row[xm];
+      b[i] = row[x0];
+    } else {
+      a[i] = row[x0 + 1];
+      b[i] = row[xp];
     }
   }
-  const real F[3] = {P.g[0], P.g[1], P.g[2]};
-  collide<real, FORCE>(a, F, P);
-  collide<real, FORCE>(b, F, P);
+}
+
+template <typename real>
+__device__ __forceinline__ void store_pair(real *__restrict__ fout, const LatParams<real> &P,
+                                           size_t n, const real a[Q], const real b[Q]) {
+  using V2 = typename Vec2<real>::T;
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     V2 v;
@@ -257,33 +245,59 @@ __global__ void __launch_bounds__(128) stream_collide_kernel(const real *__restr
   }
 }
 
+// K1: fused stream-collide of every fluid node with the uniform body force only (FORCE: the
+// body force is non-zero). The nodes of active interface tiles are collided again by K1t with
+// their interface force, so this pass does not wait for the interface chain of the step.
+// Each thread owns the two nodes (x0, x0 + 1), x0 even: populations that do not move along x
+// and every store are one aligned 2-wide access, and the address arithmetic is shared.
+template <typename real, bool FIRST, bool FORCE>
+__global__ void __launch_bounds__(128) stream_collide_kernel(const real *__restrict__ fin,
+                                                             real *__restrict__ fout,
+                                                             const LatParams<real> P, int z0) {
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y;
+  const int z = blockIdx.z + z0;
+  if (x0 >= P.nx) return;
+  real a[Q], b[Q];  // populations of nodes x0 and x0 + 1
+  load_pair<real, FIRST>(fin, P, x0, y, z, a, b);
+  const real F[3] = {P.g[0], P.g[1], P.g[2]};
+  collide<real, FORCE>(a, F, P);
+  collide<real, FORCE>(b, F, P);
+  store_pair(fout, P, (size_t)z * P.nx * P.ny + (size_t)y * P.nx + x0, a, b);
+}
+
 // K1t: stream-collide of the fluid nodes of the active tiles with body + interface force,
-// one 64-thread block per tile (grid-stride). Runs after K1 of the same step and overwrites
-// those nodes.
+// one warp per tile (grid-stride), each thread the node pair (x0, x0 + 1) of a tile row as in
+// K1. Runs after K1 of the same step and overwrites those nodes. Pairs whose interface force
+// is zero keep K1's result, which is already the post-collision state with the body force
+// alone.
 template <typename real, bool FIRST>
-__global__ void __launch_bounds__(64) stream_collide_tiles_kernel(
+__global__ void __launch_bounds__(128) stream_collide_tiles_kernel(
     const real *__restrict__ fin, real *__restrict__ fout, const int *__restrict__ slot_tile,
     const int *__restrict__ nslots_ptr, const Vec4<real> *__restrict__ Fslot,
     const LatParams<real> P, int max_slots) {
   const int nslots = min(*nslots_ptr, max_slots);
-  const int cell = threadIdx.x;
-  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int px = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
+  const int cell = 16 * lz + 4 * ly + 2 * px;
+  const int warps = blockDim.x >> 5;
+  for (int s = blockIdx.x * warps + (threadIdx.x >> 5); s < nslots; s += gridDim.x * warps) {
+    const Vec4<real> Fa = Fslot[(size_t)s * TILE_CELLS + cell];
+    const Vec4<real> Fb = Fslot[(size_t)s * TILE_CELLS + cell + 1];
     const int t = slot_tile[s];
     const int tx = t % P.ntx, ty = (t / P.ntx) % P.nty, tz = t / (P.ntx * P.nty);
-    const int x = tx * TILE + (cell & 3), y = ty * TILE + ((cell >> 2) & 3),
-              z = tz * TILE + (cell >> 4);
+    const int x0 = tx * TILE + 2 * px, y = ty * TILE + ly, z = tz * TILE + lz;
     if (z >= P.nz || (P.has_walls && (z == 0 || z == P.nz - 1))) continue;
-    const size_t n = ((size_t)z * P.ny + y) * P.nx + x;
-    real f[Q];
-    if (FIRST) {
-#pragma unroll
-      for (int i = 0; i < Q; i++) f[i] = fin[(size_t)i * P.ncell + n];
-    } else {
-      pull(fin, P, x, y, z, f);
-    }
-    const Vec4<real> Fs = Fslot[(size_t)s * TILE_CELLS + cell];
-    const real F[3] = {P.g[0] + Fs.x, P.g[1] + Fs.y, P.g[2] + Fs.z};
-    collide_store<real, true>(f, F, fout, n, P);
+    if (Fa.x == real(0) && Fa.y == real(0) && Fa.z == real(0) && Fb.x == real(0) &&
+        Fb.y == real(0) && Fb.z == real(0))
+      continue;
+    real a[Q], b[Q];
+    load_pair<real, FIRST>(fin, P, x0, y, z, a, b);
+    const real FA[3] = {P.g[0] + Fa.x, P.g[1] + Fa.y, P.g[2] + Fa.z};
+    const real FB[3] = {P.g[0] + Fb.x, P.g[1] + Fb.y, P.g[2] + Fb.z};
+    collide<real, true>(a, FA, P);
+    collide<real, true>(b, FB, P);
+    store_pair(fout, P, (size_t)z * P.nx * P.ny + (size_t)y * P.nx + x0, a, b);
   }
 }
 
@@ -439,17 +453,17 @@ cudaError_t stream_collide_t(Ctx &c, int first, cudaStream_t st) {
 template <typename real>
 cudaError_t stream_collide_tiles_t(Ctx &c, int first, cudaStream_t st) {
   const LatParams<real> P = lat_params<real>(c);
-  int grid = c.sm_count * 32;  // one tile per block for up to ~4900 active tiles
-  if (grid > c.max_slots) grid = c.max_slots;
+  int grid = c.sm_count * 8;  // 4 tiles per block: up to ~4900 active tiles in one pass
+  if (4 * grid > c.max_slots) grid = (c.max_slots + 3) / 4;
   if (grid < 1) grid = 1;
   const real *fin = (const real *)c.f[c.cur];
   real *fout = (real *)c.f[c.cur ^ 1];
   if (first)
-    stream_collide_tiles_kernel<real, true><<<grid, TILE_CELLS, 0, st>>>(
+    stream_collide_tiles_kernel<real, true><<<grid, 128, 0, st>>>(
         fin, fout, c.slot_tile[c.map], c.counters + c.map, (const Vec4<real> *)c.Fslot[c.map], P,
         c.max_slots);
   else
-    stream_collide_tiles_kernel<real, false><<<grid, TILE_CELLS, 0, st>>>(
+    stream_collide_tiles_kernel<real, false><<<grid, 128, 0, st>>>(
         fin, fout, c.slot_tile[c.map], c.counters + c.map, (const Vec4<real> *)c.Fslot[c.map], P,
         c.max_slots);
   return cudaGetLastError();

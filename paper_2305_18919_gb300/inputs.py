@@ -171,6 +171,16 @@ def shear_256_fp32(seed: int = 2305) -> Workload:
         extra={"alpha_bar": abar})
 
 
+def shear_256_fp32_box(n: int = 128, seed: int = 2305) -> Workload:
+    """The 256^3 shear workload's particle and walls in an n^3 box (profiling case: the
+    interface kernels at full mesh size on a smaller lattice, still larger than L2)."""
+    wl = shear_256_fp32(seed)
+    wl.name = f"{wl.name}_box{n}"
+    wl.nx = wl.ny = wl.nz = n
+    wl.centre = (n / 2, n / 2, n / 2 - 0.5)
+    return wl
+
+
 def scaled_shear(n: int, subdivisions: int, radius: float, tau: float = 1.0,
                  wall_u: float = 0.01, alpha=(0.01, 0.0, 0.0), precision: str = "fp32",
                  nx: int | None = None, ny: int | None = None) -> Workload:
