@@ -192,7 +192,7 @@ def k1_traffic_per_node():
     """DRAM bytes (read + write) per fluid node of one stream-collide launch, from the committed
     ncu summary, if it was taken on the current kernel source; else None."""
     import re
-    path = os.path.join(ROOT, "profiles", "stream_collide_kernel_box128.md")
+    path = os.path.join(ROOT, "profiles", "stream_collide_kernel_shear256.md")
     try:
         text = open(path).read()
     except OSError:
@@ -280,7 +280,7 @@ def run_gpu(args, wl, rank, world):
                 "step_frac": round(bpc * fluid / (ms_step * 1e-3) / 1e9 / peak, 4)}
     per_node = k1_traffic_per_node()
     if per_node is not None:
-        # measured on the 128^3 profiling case, scaled to this launch by its fluid nodes
+        # measured at full size on the 256^3 workload, per fluid node (scaled for others)
         roofline["traffic"] = int(round(per_node * fluid))
     clocks = clk.summary()
     ib_sms = lat.interface_sms()
