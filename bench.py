@@ -204,6 +204,22 @@ def k1_traffic_per_node():
     return float(m.group(1))
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest of the ranks' values (each rank's own value without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(world: int, cells: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each advanced `cells` nodes `steps` times
+    in at most `seconds` (the slowest rank's time)."""
+    return world * cells * steps / seconds / 1e6
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     from paper_2305_18919_gb300 import binding
@@ -234,13 +250,11 @@ def run_gpu(args, wl, rank, world):
     ms_total = ev0.elapsed_time(ev1)
     k1_ms, k1_launches, launches = lat.profile()
     lat.set_profiling(False)
+    ms_total = max_over_ranks(ms_total, dist, "cuda")
     if dist:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
         dist.barrier()
     ms_step = ms_total / args.steps
-    value = world * wl.cells * args.steps / (ms_total * 1e-3) / 1e6
+    value = replica_mlups(world, wl.cells, args.steps, ms_total * 1e-3)
 
     # --- end to end through the C ABI with host buffers -------------------------------------
     nv = lat.nv
@@ -256,12 +270,8 @@ def run_gpu(args, wl, rank, world):
         lat.step(1)
         lat.vertices(out=q_host)   # D2H: the step's result
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * wl.cells * e2e_steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = replica_mlups(world, wl.cells, e2e_steps, e2e_s)
 
     bpc = lat.bytes_per_cell()
     fluid = wl.nx * wl.ny * (wl.nz - 2)
