@@ -220,6 +220,37 @@ def replica_mlups(world: int, cells: int, steps: int, seconds: float) -> float:
     return world * cells * steps / seconds / 1e6
 
 
+def time_variant(wl, precision, steps, warmup):
+    """Device-timed throughput of the same workload with another population storage type
+    (inputs resident, CUDA events on the caller's stream, same step as the headline)."""
+    import torch
+    from paper_2305_18919_gb300 import binding
+    lat = binding.Lattice.from_workload(wl, precision=precision)
+    lat.step(max(3, warmup))
+    lat.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    lat.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    k1_ms, k1_launches, _ = lat.profile()
+    bpc = lat.bytes_per_cell()
+    sms = lat.interface_sms()
+    lat.close()
+    fluid = wl.nx * wl.ny * (wl.nz - 2)
+    peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    k1_avg = k1_ms / max(1, k1_launches)
+    return {"value": round(replica_mlups(1, wl.cells, steps, ms * 1e-3), 1),
+            "ms_per_step": round(ms / steps, 5), "steps": steps, "bytes_per_cell": bpc,
+            "k1_ms_avg": round(k1_avg, 5),
+            "k1_frac": round(bpc * fluid / (k1_avg * 1e-3) / 1e9 / peak, 4),
+            "interface_sms": sms}
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     from paper_2305_18919_gb300 import binding
@@ -232,6 +263,7 @@ def run_gpu(args, wl, rank, world):
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     lat = binding.Lattice.from_workload(wl, precision=wl.precision, ib_sms=args.ib_sms)
+    storage = {"fp64": "double", "fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}
     lat.step(max(3, args.warmup))
     torch.cuda.synchronize()
 
@@ -284,17 +316,24 @@ def run_gpu(args, wl, rank, world):
     achieved = bpc * fluid / (k1_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "stream_collide_kernel<float,false,false>",
+                "kernel": f"stream_collide_kernel<{'double' if wl.precision == 'fp64' else 'float'},"
+                          f"{storage[wl.precision]},false,false>",
                 "algorithmic_bytes_per_launch": bpc * fluid,
                 "k1_ms_avg": round(k1_avg_ms, 5), "peak_source": peak_note,
                 "step_frac": round(bpc * fluid / (ms_step * 1e-3) / 1e9 / peak, 4)}
-    per_node = k1_traffic_per_node()
+    per_node = k1_traffic_per_node() if wl.precision == "fp32" else None
     if per_node is not None:
         # measured at full size on the 256^3 workload, per fluid node (scaled for others)
         roofline["traffic"] = int(round(per_node * fluid))
     clocks = clk.summary()
     ib_sms = lat.interface_sms()
     lat.close()
+    variants = None
+    if rank == 0 and world == 1 and args.variant_steps > 0 and wl.precision == "fp32":
+        variants = {p: time_variant(wl, p, args.variant_steps, args.warmup)
+                    for p in ("fp16", "bf16")}
+        variants["note"] = ("populations stored in 16 bits as (f_i - w_i rho0) K / w_i, FP32 "
+                            "collision; errors against the FP64 oracle in tests/test_gpu_precision.py")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -303,7 +342,8 @@ def run_gpu(args, wl, rank, world):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 5),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if wl.precision == "fp64" else "f32",
         "data": "synthetic", "config": dict(config_of(wl), interface_sms=ib_sms),
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -312,6 +352,8 @@ def run_gpu(args, wl, rank, world):
                 "path": "iblb_set_vertices + iblb_step(1) + iblb_read_vertices, pinned host buffers"},
         "gpu_launches": int(launches), "clocks": clocks,
     }
+    if variants:
+        line["precision_variants"] = variants
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -325,6 +367,12 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="shear256")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--variant-steps", type=int, default=1000,
+                    help="steps timed for each 16-bit storage variant reported beside the FP32 "
+                         "headline (0: skip)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp16", "bf16"],
+                    help="population storage (default: the workload's; fp16/bf16 keep FP32 "
+                         "arithmetic)")
     ap.add_argument("--ib-sms", type=int, default=0,
                     help="SMs for the interface chain (0: library default, <0: no partition)")
     args = ap.parse_args()
@@ -333,6 +381,9 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     wl = workload(args.workload)
+    if args.precision and args.impl != "reference":
+        wl.precision = args.precision
+        wl.name = f"{wl.name}_{args.precision}" if args.precision not in wl.name else wl.name
     if args.impl == "reference":
         run_reference(args, wl, rank)
     else:

@@ -47,17 +47,21 @@ extern "C" {
 #define IBLB_FP64 1 /* populations and interface arithmetic in double */
 #define IBLB_FP32 2 /* populations (stored as f_i - w_i rho0) and interface forces in float;
                        vertex positions and the volume sum stay in double */
+#define IBLB_FP16 3 /* as IBLB_FP32, but populations stored in IEEE half precision as
+                       (f_i - w_i rho0) * 1024 / w_i; collision and forcing in float */
+#define IBLB_BF16 4 /* as IBLB_FP16 with bfloat16 storage of (f_i - w_i rho0) / w_i */
 
 typedef struct iblb_ctx iblb_ctx;
 
 /* Lattice description (Sec. III; walls: Sec. III last paragraph; moving walls: Sec. IV). */
 typedef struct {
   int32_t nx, ny, nz;      /* nx, ny multiples of 4; nz >= 3 with walls, >= 4 periodic */
-  int32_t precision;       /* IBLB_FP64 or IBLB_FP32 */
+  int32_t precision;       /* IBLB_FP64, IBLB_FP32, IBLB_FP16 or IBLB_BF16 */
   int32_t z_periodic;      /* 0: bounce-back walls at both z ends; 1: periodic z (tests) */
   int32_t ib_sms;          /* SMs given to the interface chain of iblb_step as a partition of
                               the GPU (green context); the stream-collide passes get the rest.
-                              0: 32 (rounded to the device's partition granularity), < 0: no
+                              0: 32, or 40 with 16-bit storage (rounded to the device's
+                              partition granularity), < 0: no
                               partition (both share all SMs, interface stream at top priority).
                               If the device or driver cannot partition, no partition is used. */
   double tau;              /* BGK relaxation time, > 1/2 (viscosity (tau - 1/2)/3) */
@@ -179,7 +183,8 @@ int iblb_mesh_volume_noalloc(const double *q_dev, const int32_t *faces_dev, int3
 int32_t iblb_interface_sms(const iblb_ctx *ctx);
 
 /* Bytes moved per fluid cell by one stream-collide launch (19 loads + 19 stores of the
-   population type): 152 for IBLB_FP32, 304 for IBLB_FP64. */
+   population storage type): 304 for IBLB_FP64, 152 for IBLB_FP32, 76 for IBLB_FP16 and
+   IBLB_BF16. */
 int64_t iblb_bytes_per_cell(const iblb_ctx *ctx);
 
 #ifdef __cplusplus

@@ -21,8 +21,10 @@ IBLB_EUNSTABLE = -4
 IBLB_ECAPACITY = -5
 IBLB_FP64 = 1
 IBLB_FP32 = 2
+IBLB_FP16 = 3
+IBLB_BF16 = 4
 
-_PRECISION = {"fp64": IBLB_FP64, "fp32": IBLB_FP32}
+_PRECISION = {"fp64": IBLB_FP64, "fp32": IBLB_FP32, "fp16": IBLB_FP16, "bf16": IBLB_BF16}
 
 
 class iblb_lattice_desc(ctypes.Structure):

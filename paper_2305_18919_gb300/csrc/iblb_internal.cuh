@@ -65,7 +65,8 @@ struct Ctx {
   int nx = 0, ny = 0, nz = 0, precision = 0, has_walls = 1;
   double tau = 1.0, rho0 = 1.0, ub[3] = {0, 0, 0}, ut[3] = {0, 0, 0}, g[3] = {0, 0, 0};
   size_t ncell = 0;
-  size_t real_size = 4;
+  size_t real_size = 4;  // interface arithmetic type (force, velocity, stencil buffers)
+  size_t pop_size = 4;   // population storage type
   void *f[2] = {nullptr, nullptr};  // populations f_i - w_i rho0, [19][nz][ny][nx]
   int cur = 0;                      // f[cur] holds the state
   int fresh = 1;                    // state is post-streaming (no collision done yet)

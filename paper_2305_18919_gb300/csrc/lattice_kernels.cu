@@ -6,7 +6,11 @@
 // [19][nz][ny][nx] with x fastest. The state array holds post-collision populations of
 // the previous step; a pull reads f_i(x - c_i) from it, which is the streaming step.
 // Right after initialisation the state holds post-streaming populations ("fresh") and the
-// first collision reads them in place.
+// first collision reads them in place. The storage type S may be narrower than the
+// arithmetic type `real` (FP16 / BF16 storage with FP32 arithmetic), see Storage below.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "iblb_internal.cuh"
 
 namespace iblb {
@@ -44,11 +48,95 @@ LatParams<real> lat_params(const Ctx &c) {
   return p;
 }
 
+// Storage of the shifted populations. Population i is stored as g_i = (f_i - w_i rho0) k_i
+// in type S and used as f_i - w_i rho0 in type `real`. For float and double k_i = 1. For the
+// 16-bit types (arithmetic stays FP32) k_i = K / w_i: the deviations of the 19 directions
+// then share one scale, about |drho| + 3 |c.u|, and with K = 1024 the FP16 values sit well
+// inside its normal range (6.1e-5 .. 65504), so each keeps FP16's 11-bit significand. BF16
+// has FP32's exponent range and needs no shift (K = 1).
+template <typename S>
+struct Storage;
+template <>
+struct Storage<double> {
+  using V2 = double2;
+  static constexpr double K = 0.0;  // 0: stored unscaled
+};
+template <>
+struct Storage<float> {
+  using V2 = float2;
+  static constexpr double K = 0.0;
+};
+template <>
+struct Storage<__half> {
+  using V2 = __half2;
+  static constexpr double K = 1024.0;
+};
+template <>
+struct Storage<__nv_bfloat16> {
+  using V2 = __nv_bfloat162;
+  static constexpr double K = 1.0;
+};
+
+// k_i and 1 / k_i
+template <typename S>
+__host__ __device__ constexpr double kscale(int i) {
+  return Storage<S>::K == 0.0 ? 1.0 : Storage<S>::K / wgt(i);
+}
+template <typename S>
+__host__ __device__ constexpr double kinv(int i) {
+  return Storage<S>::K == 0.0 ? 1.0 : wgt(i) / Storage<S>::K;
+}
+
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(__half v) { return __half2float(v); }
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ void widen2(float2 v, float &a, float &b) { a = v.x; b = v.y; }
+__device__ __forceinline__ void widen2(double2 v, double &a, double &b) { a = v.x; b = v.y; }
+__device__ __forceinline__ void widen2(__half2 v, float &a, float &b) {
+  a = __low2float(v);
+  b = __high2float(v);
+}
+__device__ __forceinline__ void widen2(__nv_bfloat162 v, float &a, float &b) {
+  a = __low2float(v);
+  b = __high2float(v);
+}
+
+// Rounding of `real` values to the storage type (round to nearest even).
+template <typename S>
+struct Narrow;
+template <>
+struct Narrow<float> {
+  __device__ static float one(float v) { return v; }
+  __device__ static float2 two(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct Narrow<double> {
+  __device__ static double one(double v) { return v; }
+  __device__ static double2 two(double a, double b) { return make_double2(a, b); }
+};
+template <>
+struct Narrow<__half> {
+  __device__ static __half one(float v) { return __float2half_rn(v); }
+  __device__ static __half2 two(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <>
+struct Narrow<__nv_bfloat16> {
+  __device__ static __nv_bfloat16 one(float v) { return __float2bfloat16_rn(v); }
+  __device__ static __nv_bfloat162 two(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
+// The deviation f_i - w_i rho0 stored at element `idx` of array p (population i).
+template <typename real, typename S>
+__device__ __forceinline__ real dev(const S *__restrict__ p, int i, size_t idx) {
+  return real(widen(p[idx])) * real(kinv<S>(i));
+}
+
 // Pull the 19 post-streaming populations of fluid node (x, y, z) from post-collision array
 // `fp`. A link whose source is a wall node is bounced back: the opposite post-collision
 // population of the same node plus the moving-wall term.
-template <typename real>
-__device__ __forceinline__ void pull(const real *__restrict__ fp, const LatParams<real> &P, int x,
+template <typename real, typename S>
+__device__ __forceinline__ void pull(const S *__restrict__ fp, const LatParams<real> &P, int x,
                                      int y, int z, real f[Q]) {
   const int xm = x == 0 ? P.nx - 1 : x - 1, xp = x == P.nx - 1 ? 0 : x + 1;
   const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
@@ -67,13 +155,12 @@ __device__ __forceinline__ void pull(const real *__restrict__ fp, const LatParam
   const size_t n = zo[1] + yo[1] + x;
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    const real *fi = fp + (size_t)i * P.ncell;
     if (cz(i) > 0 && wall_below) {
-      f[i] = fp[(size_t)opp(i) * P.ncell + n] + P.wb[i];
+      f[i] = dev<real>(fp, opp(i), (size_t)opp(i) * P.ncell + n) + P.wb[i];
     } else if (cz(i) < 0 && wall_above) {
-      f[i] = fp[(size_t)opp(i) * P.ncell + n] + P.wt[i];
+      f[i] = dev<real>(fp, opp(i), (size_t)opp(i) * P.ncell + n) + P.wt[i];
     } else {
-      f[i] = fi[zo[1 - cz(i)] + yo[1 - cy(i)] + xo[1 - cx(i)]];
+      f[i] = dev<real>(fp, i, (size_t)i * P.ncell + zo[1 - cz(i)] + yo[1 - cy(i)] + xo[1 - cx(i)]);
     }
   }
 }
@@ -165,34 +252,23 @@ __device__ __forceinline__ void collide(real f[Q], const real F[3], const LatPar
   }
 }
 
-template <typename real>
-struct Vec2;
-template <>
-struct Vec2<float> {
-  using T = float2;
-};
-template <>
-struct Vec2<double> {
-  using T = double2;
-};
-
 // Post-streaming populations a (node x0) and b (node x0 + 1) of two fluid nodes, x0 even,
 // from post-collision array `fin` (FIRST: `fin` already holds post-streaming populations,
 // read in place). Populations that do not move along x are one aligned 2-wide load; a link
 // whose source is a wall node is bounced back (opposite population of the same node plus the
 // moving-wall term).
-template <typename real, bool FIRST>
-__device__ __forceinline__ void load_pair(const real *__restrict__ fin, const LatParams<real> &P,
+template <typename real, typename S, bool FIRST>
+__device__ __forceinline__ void load_pair(const S *__restrict__ fin, const LatParams<real> &P,
                                           int x0, int y, int z, real a[Q], real b[Q]) {
-  using V2 = typename Vec2<real>::T;
+  using V2 = typename Storage<S>::V2;
   const size_t plane = (size_t)P.nx * P.ny;
   const size_t n = (size_t)z * plane + (size_t)y * P.nx + x0;
   if (FIRST) {
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-      const V2 v = *reinterpret_cast<const V2 *>(fin + (size_t)i * P.ncell + n);
-      a[i] = v.x;
-      b[i] = v.y;
+      widen2(*reinterpret_cast<const V2 *>(fin + (size_t)i * P.ncell + n), a[i], b[i]);
+      a[i] *= real(kinv<S>(i));
+      b[i] *= real(kinv<S>(i));
     }
     return;
   }
@@ -211,38 +287,35 @@ __device__ __forceinline__ void load_pair(const real *__restrict__ fin, const La
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     if ((cz(i) > 0 && wall_below) || (cz(i) < 0 && wall_above)) {
-      const V2 v = *reinterpret_cast<const V2 *>(fin + (size_t)opp(i) * P.ncell + n);
+      widen2(*reinterpret_cast<const V2 *>(fin + (size_t)opp(i) * P.ncell + n), a[i], b[i]);
       const real wall = cz(i) > 0 ? P.wb[i] : P.wt[i];
-      a[i] = v.x + wall;
-      b[i] = v.y + wall;
+      a[i] = a[i] * real(kinv<S>(opp(i))) + wall;
+      b[i] = b[i] * real(kinv<S>(opp(i))) + wall;
       continue;
     }
-    const real *row = fin + (size_t)i * P.ncell + zo[1 - cz(i)] + yo[1 - cy(i)];
+    const S *row = fin + (size_t)i * P.ncell + zo[1 - cz(i)] + yo[1 - cy(i)];
     if (cx(i) == 0) {
-      const V2 v = *reinterpret_cast<const V2 *>(row + x0);
-      a[i] = v.x;
-      b[i] = v.y;
+      widen2(*reinterpret_cast<const V2 *>(row + x0), a[i], b[i]);
     } else if (cx(i) > 0) {
-      a[i] = row[xm];
-      b[i] = row[x0];
+      a[i] = widen(row[xm]);
+      b[i] = widen(row[x0]);
     } else {
-      a[i] = row[x0 + 1];
-      b[i] = row[xp];
+      a[i] = widen(row[x0 + 1]);
+      b[i] = widen(row[xp]);
     }
+    a[i] *= real(kinv<S>(i));
+    b[i] *= real(kinv<S>(i));
   }
 }
 
-template <typename real>
-__device__ __forceinline__ void store_pair(real *__restrict__ fout, const LatParams<real> &P,
+template <typename real, typename S>
+__device__ __forceinline__ void store_pair(S *__restrict__ fout, const LatParams<real> &P,
                                            size_t n, const real a[Q], const real b[Q]) {
-  using V2 = typename Vec2<real>::T;
+  using V2 = typename Storage<S>::V2;
 #pragma unroll
-  for (int i = 0; i < Q; i++) {
-    V2 v;
-    v.x = a[i];
-    v.y = b[i];
-    *reinterpret_cast<V2 *>(fout + (size_t)i * P.ncell + n) = v;
-  }
+  for (int i = 0; i < Q; i++)
+    *reinterpret_cast<V2 *>(fout + (size_t)i * P.ncell + n) =
+        Narrow<S>::two(a[i] * real(kscale<S>(i)), b[i] * real(kscale<S>(i)));
 }
 
 // K1: fused stream-collide of every fluid node with the uniform body force only (FORCE: the
@@ -250,20 +323,215 @@ __device__ __forceinline__ void store_pair(real *__restrict__ fout, const LatPar
 // their interface force, so this pass does not wait for the interface chain of the step.
 // Each thread owns the two nodes (x0, x0 + 1), x0 even: populations that do not move along x
 // and every store are one aligned 2-wide access, and the address arithmetic is shared.
-template <typename real, bool FIRST, bool FORCE>
-__global__ void __launch_bounds__(128) stream_collide_kernel(const real *__restrict__ fin,
-                                                             real *__restrict__ fout,
+template <typename real, typename S, bool FIRST, bool FORCE>
+__global__ void __launch_bounds__(128) stream_collide_kernel(const S *__restrict__ fin,
+                                                             S *__restrict__ fout,
                                                              const LatParams<real> P, int z0) {
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y;
   const int z = blockIdx.z + z0;
   if (x0 >= P.nx) return;
   real a[Q], b[Q];  // populations of nodes x0 and x0 + 1
-  load_pair<real, FIRST>(fin, P, x0, y, z, a, b);
+  load_pair<real, S, FIRST>(fin, P, x0, y, z, a, b);
   const real F[3] = {P.g[0], P.g[1], P.g[2]};
   collide<real, FORCE>(a, F, P);
   collide<real, FORCE>(b, F, P);
   store_pair(fout, P, (size_t)z * P.nx * P.ny + (size_t)y * P.nx + x0, a, b);
+}
+
+// Two-wide FP32 arithmetic (one packed instruction per operation on sm_100 and later):
+// lane x belongs to the first node of a pair, lane y to the second.
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, dup(-1.0f), a); }
+
+// BGK collision with Guo forcing (Eqs. 9-10) of a node pair held in the scaled storage units
+// of a 16-bit type, g_i = (f_i - w_i rho0) K / w_i. The moments weigh g_i by w_i / K, and the
+// update is the one of `collide` multiplied through by k_i = K / w_i, where the weights cancel:
+//   g*_i = g_i + omega (K [drho + rho (4.5 (c.u)^2 - 1.5 u^2) +- 3 rho (c.u)] - g_i)
+//          + K (1 - 1/2tau) [9 (c.F)(c.u) - 3 u.F +- 3 (c.F)]
+// (F uniform over the pair). rho is rounded once here: the storage rounding of the 16-bit
+// types is four orders of magnitude above it.
+template <bool FORCE>
+__device__ __forceinline__ void collide_pair_scaled(float2 g[Q], const float F[3],
+                                                    const LatParams<float> &P, float K) {
+  const float iK = 1.0f / K;
+  float2 drho = mul2(g[0], dup(float(wgt(0)) * iK));
+  float2 jx = dup(0.0f), jy = dup(0.0f), jz = dup(0.0f);
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const float2 w = dup(float(wgt(i)) * iK);
+    drho = fma2(add2(g[i], g[i + 1]), w, drho);
+    const float2 d = mul2(sub2(g[i], g[i + 1]), w);
+    if (cx(i)) jx = cx(i) > 0 ? add2(jx, d) : sub2(jx, d);
+    if (cy(i)) jy = cy(i) > 0 ? add2(jy, d) : sub2(jy, d);
+    if (cz(i)) jz = cz(i) > 0 ? add2(jz, d) : sub2(jz, d);
+  }
+  const float2 rho = add2(dup(P.rho0), drho);
+  const float2 inv_rho = make_float2(__frcp_rn(rho.x), __frcp_rn(rho.y));
+  float2 ux = jx, uy = jy, uz = jz;
+  if (FORCE) {
+    ux = fma2(dup(0.5f), dup(F[0]), ux);
+    uy = fma2(dup(0.5f), dup(F[1]), uy);
+    uz = fma2(dup(0.5f), dup(F[2]), uz);
+  }
+  ux = mul2(ux, inv_rho);
+  uy = mul2(uy, inv_rho);
+  uz = mul2(uz, inv_rho);
+  const float2 uu15 = mul2(dup(1.5f), fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
+  const float2 om = dup(P.omega), omc = dup(1.0f - P.omega);
+  const float2 Kdrho = mul2(dup(K), drho), Krho = mul2(dup(K), rho);
+  const float2 Krho3 = mul2(dup(3.0f), Krho);
+  float2 KuF3 = dup(0.0f);
+  const float Kguo = K * P.guo;
+  if (FORCE)
+    KuF3 = mul2(dup(3.0f * Kguo),
+                fma2(ux, dup(F[0]), fma2(uy, dup(F[1]), mul2(uz, dup(F[2])))));
+  {  // rest population: g*_0 = (1 - omega) g_0 + omega K (drho - rho 1.5 u^2) - K guo 3 u.F
+    const float2 feq = sub2(Kdrho, mul2(Krho, uu15));
+    float2 out = fma2(omc, g[0], mul2(om, feq));
+    if (FORCE) out = sub2(out, KuF3);
+    g[0] = out;
+  }
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    float2 cu = dup(0.0f);
+    if (cx(i)) cu = cx(i) > 0 ? add2(cu, ux) : sub2(cu, ux);
+    if (cy(i)) cu = cy(i) > 0 ? add2(cu, uy) : sub2(cu, uy);
+    if (cz(i)) cu = cz(i) > 0 ? add2(cu, uz) : sub2(cu, uz);
+    const float2 xs = fma2(mul2(dup(4.5f), cu), cu, mul2(dup(-1.0f), uu15));
+    const float2 sym = fma2(Krho, xs, Kdrho);
+    const float2 asym = mul2(Krho3, cu);
+    float2 a = fma2(omc, g[i], mul2(om, add2(sym, asym)));
+    float2 b = fma2(omc, g[i + 1], mul2(om, sub2(sym, asym)));
+    if (FORCE) {
+      const float cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
+      const float2 ssym = sub2(mul2(dup(9.0f * Kguo * cF), cu), KuF3);
+      const float2 sasym = dup(3.0f * Kguo * cF);
+      a = add2(a, add2(ssym, sasym));
+      b = add2(b, sub2(ssym, sasym));
+    }
+    g[i] = a;
+    g[i + 1] = b;
+  }
+}
+
+template <typename V2>
+__device__ __forceinline__ float2 widen_pair(V2 v);
+template <>
+__device__ __forceinline__ float2 widen_pair(__half2 v) { return __half22float2(v); }
+template <>
+__device__ __forceinline__ float2 widen_pair(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <typename V2>
+__device__ __forceinline__ V2 narrow_pair(float2 v);
+template <>
+__device__ __forceinline__ __half2 narrow_pair(float2 v) { return __float22half2_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat162 narrow_pair(float2 v) { return __float22bfloat162_rn(v); }
+
+// Reinterpret 32 bits as a pair of 16-bit storage values, and back.
+template <typename V2>
+__device__ __forceinline__ V2 as_pair(unsigned int u) {
+  V2 v;
+  memcpy(&v, &u, sizeof(v));
+  return v;
+}
+template <typename V2>
+__device__ __forceinline__ unsigned int as_bits(V2 v) {
+  unsigned int u;
+  memcpy(&u, &v, sizeof(u));
+  return u;
+}
+
+// K1 for 16-bit storage: each thread owns four nodes x0 .. x0 + 3 (x0 a multiple of 4), so
+// every population row is one aligned 8-byte load (plus one 2-byte load of the neighbouring
+// node for the directions that move along x) and every store one 8-byte store: half the
+// memory instructions of the two-node form and twice the bytes in flight per thread, which a
+// 2-byte type needs to keep HBM busy. The loaded rows stay packed in registers (`lo` holds
+// nodes x0, x0 + 1, `hi` nodes x0 + 2, x0 + 3) and are widened one node pair at a time for
+// the collision; the results are packed back in place.
+template <typename S, bool FIRST, bool FORCE>
+__global__ void __launch_bounds__(128) stream_collide_quad_kernel(const S *__restrict__ fin,
+                                                                  S *__restrict__ fout,
+                                                                  const LatParams<float> P,
+                                                                  int z0) {
+  using V2 = typename Storage<S>::V2;
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y;
+  const int z = blockIdx.z + z0;
+  if (x0 >= P.nx) return;
+  const size_t plane = (size_t)P.nx * P.ny;
+  const size_t n = (size_t)z * plane + (size_t)y * P.nx + x0;
+  unsigned int lo[Q], hi[Q];  // packed pairs (x0, x0 + 1) and (x0 + 2, x0 + 3)
+  bool bounced[Q];            // population i comes from the wall: add the wall term
+  if (FIRST) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const uint2 v = *reinterpret_cast<const uint2 *>(fin + (size_t)i * P.ncell + n);
+      lo[i] = v.x;
+      hi[i] = v.y;
+      bounced[i] = false;
+    }
+  } else {
+    const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;   // source of node x0 for c_x = +1
+    const int xp = x0 + 4 == P.nx ? 0 : x0 + 4;   // source of node x0 + 3 for c_x = -1
+    const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
+    int zm = z - 1, zp = z + 1;
+    if (!P.has_walls) {
+      zm = z == 0 ? P.nz - 1 : zm;
+      zp = z == P.nz - 1 ? 0 : zp;
+    }
+    const bool wall_below = P.has_walls && zm == 0;
+    const bool wall_above = P.has_walls && zp == P.nz - 1;
+    const size_t zo[3] = {(size_t)zm * plane, (size_t)z * plane, (size_t)zp * plane};
+    const size_t yo[3] = {(size_t)ym * P.nx, (size_t)y * P.nx, (size_t)yp * P.nx};
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      bounced[i] = (cz(i) > 0 && wall_below) || (cz(i) < 0 && wall_above);
+      if (bounced[i]) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(fin + (size_t)opp(i) * P.ncell + n);
+        lo[i] = v.x;
+        hi[i] = v.y;
+        continue;
+      }
+      const S *row = fin + (size_t)i * P.ncell + zo[1 - cz(i)] + yo[1 - cy(i)];
+      const uint2 v = *reinterpret_cast<const uint2 *>(row + x0);  // nodes x0 .. x0 + 3
+      if (cx(i) == 0) {
+        lo[i] = v.x;
+        hi[i] = v.y;
+      } else if (cx(i) > 0) {  // sources x0 - 1 .. x0 + 2
+        const unsigned int e = *reinterpret_cast<const unsigned short *>(row + xm);
+        lo[i] = __byte_perm(e, v.x, 0x5410);
+        hi[i] = __byte_perm(v.x, v.y, 0x5432);
+      } else {  // sources x0 + 1 .. x0 + 4
+        const unsigned int e = *reinterpret_cast<const unsigned short *>(row + xp);
+        lo[i] = __byte_perm(v.x, v.y, 0x5432);
+        hi[i] = __byte_perm(v.y, e, 0x5432);
+      }
+    }
+  }
+  const float F[3] = {P.g[0], P.g[1], P.g[2]};
+#pragma unroll
+  for (int h = 0; h < 2; h++) {  // node pairs (x0, x0 + 1), (x0 + 2, x0 + 3)
+    unsigned int *pk = h ? hi : lo;
+    float2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      g[i] = widen_pair(as_pair<V2>(pk[i]));
+      if (bounced[i]) {  // stored units: the wall term times k_i
+        const float wall = (cz(i) > 0 ? P.wb[i] : P.wt[i]) * float(kscale<S>(i));
+        g[i] = add2(g[i], dup(wall));
+      }
+    }
+    collide_pair_scaled<FORCE>(g, F, P, float(Storage<S>::K));
+#pragma unroll
+    for (int i = 0; i < Q; i++) pk[i] = as_bits(narrow_pair<V2>(g[i]));
+  }
+#pragma unroll
+  for (int i = 0; i < Q; i++)
+    *reinterpret_cast<uint2 *>(fout + (size_t)i * P.ncell + n) = make_uint2(lo[i], hi[i]);
 }
 
 // K1t: stream-collide of the fluid nodes of the active tiles with body + interface force,
@@ -271,9 +539,9 @@ __global__ void __launch_bounds__(128) stream_collide_kernel(const real *__restr
 // K1. Runs after K1 of the same step and overwrites those nodes. Pairs whose interface force
 // is zero keep K1's result, which is already the post-collision state with the body force
 // alone.
-template <typename real, bool FIRST>
+template <typename real, typename S, bool FIRST>
 __global__ void __launch_bounds__(128) stream_collide_tiles_kernel(
-    const real *__restrict__ fin, real *__restrict__ fout, const int *__restrict__ slot_tile,
+    const S *__restrict__ fin, S *__restrict__ fout, const int *__restrict__ slot_tile,
     const int *__restrict__ nslots_ptr, const Vec4<real> *__restrict__ Fslot,
     const LatParams<real> P, int max_slots) {
   const int nslots = min(*nslots_ptr, max_slots);
@@ -292,7 +560,7 @@ __global__ void __launch_bounds__(128) stream_collide_tiles_kernel(
         Fb.y == real(0) && Fb.z == real(0))
       continue;
     real a[Q], b[Q];
-    load_pair<real, FIRST>(fin, P, x0, y, z, a, b);
+    load_pair<real, S, FIRST>(fin, P, x0, y, z, a, b);
     const real FA[3] = {P.g[0] + Fa.x, P.g[1] + Fa.y, P.g[2] + Fa.z};
     const real FB[3] = {P.g[0] + Fb.x, P.g[1] + Fb.y, P.g[2] + Fb.z};
     collide<real, true>(a, FA, P);
@@ -303,8 +571,8 @@ __global__ void __launch_bounds__(128) stream_collide_tiles_kernel(
 
 // K1b: velocity after streaming at every node of the active interface tiles.
 // One 64-thread block per active tile (grid-stride over the device-side tile count).
-template <typename real>
-__global__ void __launch_bounds__(64) shell_velocity_kernel(const real *__restrict__ fpost,
+template <typename real, typename S>
+__global__ void __launch_bounds__(64) shell_velocity_kernel(const S *__restrict__ fpost,
                                                             const int *__restrict__ slot_tile,
                                                             const int *__restrict__ nslots_ptr,
                                                             const Vec4<real> *__restrict__ Fslot,
@@ -356,8 +624,8 @@ __global__ void __launch_bounds__(64) shell_velocity_kernel(const real *__restri
 }
 
 // rho and u of every node of the current post-streaming state (read-back, not on the step).
-template <typename real>
-__global__ void fields_kernel(const real *__restrict__ fstate, int fresh,
+template <typename real, typename S>
+__global__ void fields_kernel(const S *__restrict__ fstate, int fresh,
                               const int *__restrict__ tile_slot,
                               const Vec4<real> *__restrict__ Fslot,
                               const LatParams<real> P, double3 ub, double3 ut, double rho0,
@@ -373,7 +641,7 @@ __global__ void fields_kernel(const real *__restrict__ fstate, int fresh,
   }
   real f[Q];
   if (fresh) {
-    for (int i = 0; i < Q; i++) f[i] = fstate[(size_t)i * P.ncell + n];
+    for (int i = 0; i < Q; i++) f[i] = dev<real>(fstate, i, (size_t)i * P.ncell + n);
   } else {
     pull(fstate, P, x, y, z, f);
   }
@@ -391,8 +659,8 @@ __global__ void fields_kernel(const real *__restrict__ fstate, int fresh,
   for (int k = 0; k < 3; k++) u_out[3 * n + k] = (j[k] + 0.5 * (double)F[k]) / rho;
 }
 
-template <typename real>
-__global__ void populations_kernel(const real *__restrict__ fstate, int fresh,
+template <typename real, typename S>
+__global__ void populations_kernel(const S *__restrict__ fstate, int fresh,
                                    const LatParams<real> P, double rho0,
                                    double *__restrict__ f_out) {
   const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -404,15 +672,15 @@ __global__ void populations_kernel(const real *__restrict__ fstate, int fresh,
   }
   real f[Q];
   if (fresh) {
-    for (int i = 0; i < Q; i++) f[i] = fstate[(size_t)i * P.ncell + n];
+    for (int i = 0; i < Q; i++) f[i] = dev<real>(fstate, i, (size_t)i * P.ncell + n);
   } else {
     pull(fstate, P, x, y, z, f);
   }
   for (int i = 0; i < Q; i++) f_out[(size_t)i * P.ncell + n] = wgt(i) * rho0 + (double)f[i];
 }
 
-template <typename real>
-__global__ void init_equilibrium_kernel(real *__restrict__ fstate, const LatParams<real> P,
+template <typename real, typename S>
+__global__ void init_equilibrium_kernel(S *__restrict__ fstate, const LatParams<real> P,
                                         double rho0, const double *__restrict__ rho_in,
                                         const double *__restrict__ u_in) {
   const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -425,117 +693,144 @@ __global__ void init_equilibrium_kernel(real *__restrict__ fstate, const LatPara
   for (int i = 0; i < Q; i++) {
     const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
     const double v = wgt(i) * ((rho - rho0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
-    fstate[(size_t)i * P.ncell + n] = wall ? real(0) : (real)v;
+    fstate[(size_t)i * P.ncell + n] = Narrow<S>::one(wall ? real(0) : (real)(v * kscale<S>(i)));
   }
 }
 
-template <typename real>
+template <typename S>
+cudaError_t stream_collide_quad_t(Ctx &c, int first, cudaStream_t st) {
+  const LatParams<float> P = lat_params<float>(c);
+  const int z0 = c.has_walls ? 1 : 0;
+  const int nzf = c.has_walls ? c.nz - 2 : c.nz;
+  const int quads = c.nx / 4;  // four nodes per thread along x
+  const int bx = quads < 128 ? quads : 128;
+  dim3 grid((quads + bx - 1) / bx, c.ny, nzf);
+  const S *fin = (const S *)c.f[c.cur];
+  S *fout = (S *)c.f[c.cur ^ 1];
+  const bool force = c.g[0] != 0.0 || c.g[1] != 0.0 || c.g[2] != 0.0;
+  if (first) {
+    if (force) stream_collide_quad_kernel<S, true, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    else stream_collide_quad_kernel<S, true, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+  } else {
+    if (force) stream_collide_quad_kernel<S, false, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    else stream_collide_quad_kernel<S, false, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+  }
+  return cudaGetLastError();
+}
+
+template <typename real, typename S>
 cudaError_t stream_collide_t(Ctx &c, int first, cudaStream_t st) {
+  if constexpr (sizeof(S) == 2) return stream_collide_quad_t<S>(c, first, st);
   const LatParams<real> P = lat_params<real>(c);
   const int z0 = c.has_walls ? 1 : 0;
   const int nzf = c.has_walls ? c.nz - 2 : c.nz;
   const int half = c.nx / 2;  // two nodes per thread along x
   const int bx = half < 128 ? half : 128;
   dim3 grid((half + bx - 1) / bx, c.ny, nzf);
-  const real *fin = (const real *)c.f[c.cur];
-  real *fout = (real *)c.f[c.cur ^ 1];
+  const S *fin = (const S *)c.f[c.cur];
+  S *fout = (S *)c.f[c.cur ^ 1];
   const bool force = c.g[0] != 0.0 || c.g[1] != 0.0 || c.g[2] != 0.0;
   if (first) {
-    if (force) stream_collide_kernel<real, true, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
-    else stream_collide_kernel<real, true, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    if (force) stream_collide_kernel<real, S, true, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    else stream_collide_kernel<real, S, true, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
   } else {
-    if (force) stream_collide_kernel<real, false, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
-    else stream_collide_kernel<real, false, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    if (force) stream_collide_kernel<real, S, false, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    else stream_collide_kernel<real, S, false, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
   }
   return cudaGetLastError();
 }
 
-template <typename real>
+template <typename real, typename S>
 cudaError_t stream_collide_tiles_t(Ctx &c, int first, cudaStream_t st) {
   const LatParams<real> P = lat_params<real>(c);
   int grid = c.sm_count * 8;  // 4 tiles per block: up to ~4900 active tiles in one pass
   if (4 * grid > c.max_slots) grid = (c.max_slots + 3) / 4;
   if (grid < 1) grid = 1;
-  const real *fin = (const real *)c.f[c.cur];
-  real *fout = (real *)c.f[c.cur ^ 1];
+  const S *fin = (const S *)c.f[c.cur];
+  S *fout = (S *)c.f[c.cur ^ 1];
   if (first)
-    stream_collide_tiles_kernel<real, true><<<grid, 128, 0, st>>>(
+    stream_collide_tiles_kernel<real, S, true><<<grid, 128, 0, st>>>(
         fin, fout, c.slot_tile[c.map], c.counters + c.map, (const Vec4<real> *)c.Fslot[c.map], P,
         c.max_slots);
   else
-    stream_collide_tiles_kernel<real, false><<<grid, 128, 0, st>>>(
+    stream_collide_tiles_kernel<real, S, false><<<grid, 128, 0, st>>>(
         fin, fout, c.slot_tile[c.map], c.counters + c.map, (const Vec4<real> *)c.Fslot[c.map], P,
         c.max_slots);
   return cudaGetLastError();
 }
 
-template <typename real>
+template <typename real, typename S>
 cudaError_t shell_velocity_t(Ctx &c, cudaStream_t st) {
   const LatParams<real> P = lat_params<real>(c);
   int grid = c.sm_count * 32;
   if (grid > c.max_slots) grid = c.max_slots;
   if (grid < 1) grid = 1;
-  shell_velocity_kernel<real><<<grid, TILE_CELLS, 0, st>>>(
-      (const real *)c.f[c.cur], c.slot_tile[c.map], c.counters + c.map,
+  shell_velocity_kernel<real, S><<<grid, TILE_CELLS, 0, st>>>(
+      (const S *)c.f[c.cur], c.slot_tile[c.map], c.counters + c.map,
       (const Vec4<real> *)c.Fslot[c.map], (Vec4<real> *)c.Uslot, P, (real)c.ub[0], (real)c.ub[1], (real)c.ub[2], (real)c.ut[0],
       (real)c.ut[1], (real)c.ut[2], c.max_slots);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-cudaError_t launch_stream_collide(Ctx &c, int first, cudaStream_t s) {
-  return c.precision == IBLB_FP64 ? stream_collide_t<double>(c, first, s)
-                                  : stream_collide_t<float>(c, first, s);
-}
-
-cudaError_t launch_stream_collide_tiles(Ctx &c, int first, cudaStream_t s) {
-  return c.precision == IBLB_FP64 ? stream_collide_tiles_t<double>(c, first, s)
-                                  : stream_collide_tiles_t<float>(c, first, s);
-}
-
-cudaError_t launch_shell_velocity(Ctx &c, cudaStream_t s) {
-  return c.precision == IBLB_FP64 ? shell_velocity_t<double>(c, s) : shell_velocity_t<float>(c, s);
-}
-
-cudaError_t launch_fields(Ctx &c, double *rho_dev, double *u_dev) {
+template <typename real, typename S>
+cudaError_t fields_t(Ctx &c, double *rho_dev, double *u_dev) {
   const int blocks = (int)((c.ncell + 255) / 256);
   const double3 ub = make_double3(c.ub[0], c.ub[1], c.ub[2]);
   const double3 ut = make_double3(c.ut[0], c.ut[1], c.ut[2]);
   // the force of the last spreading step lives in the map that step used
   const int *ts = (c.nv && c.have_force) ? c.tile_slot[c.map ^ 1] : nullptr;
-  if (c.precision == IBLB_FP64) {
-    fields_kernel<double><<<blocks, 256, 0, c.stream>>>(
-        (const double *)c.f[c.cur], c.fresh, ts, (const Vec4<double> *)c.Fslot[c.map ^ 1], lat_params<double>(c),
-        ub, ut, c.rho0, rho_dev, u_dev);
-  } else {
-    fields_kernel<float><<<blocks, 256, 0, c.stream>>>(
-        (const float *)c.f[c.cur], c.fresh, ts, (const Vec4<float> *)c.Fslot[c.map ^ 1], lat_params<float>(c), ub,
-        ut, c.rho0, rho_dev, u_dev);
-  }
+  fields_kernel<real, S><<<blocks, 256, 0, c.stream>>>(
+      (const S *)c.f[c.cur], c.fresh, ts, (const Vec4<real> *)c.Fslot[c.map ^ 1],
+      lat_params<real>(c), ub, ut, c.rho0, rho_dev, u_dev);
   return cudaGetLastError();
 }
 
-cudaError_t launch_populations(Ctx &c, double *f_dev) {
+template <typename real, typename S>
+cudaError_t populations_t(Ctx &c, double *f_dev) {
   const int blocks = (int)((c.ncell + 255) / 256);
-  if (c.precision == IBLB_FP64)
-    populations_kernel<double><<<blocks, 256, 0, c.stream>>>(
-        (const double *)c.f[c.cur], c.fresh, lat_params<double>(c), c.rho0, f_dev);
-  else
-    populations_kernel<float><<<blocks, 256, 0, c.stream>>>(
-        (const float *)c.f[c.cur], c.fresh, lat_params<float>(c), c.rho0, f_dev);
+  populations_kernel<real, S><<<blocks, 256, 0, c.stream>>>(
+      (const S *)c.f[c.cur], c.fresh, lat_params<real>(c), c.rho0, f_dev);
   return cudaGetLastError();
 }
+
+template <typename real, typename S>
+cudaError_t init_equilibrium_t(Ctx &c, const double *rho_dev, const double *u_dev) {
+  const int blocks = (int)((c.ncell + 255) / 256);
+  init_equilibrium_kernel<real, S><<<blocks, 256, 0, c.stream>>>(
+      (S *)c.f[c.cur], lat_params<real>(c), c.rho0, rho_dev, u_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Dispatch on the context's precision: (arithmetic, storage) = (double, double) for FP64,
+// (float, float) for FP32, (float, half) for FP16 and (float, bfloat16) for BF16.
+#define IBLB_DISPATCH(c, FN, ...)                                         \
+  switch ((c).precision) {                                                \
+    case IBLB_FP64: return FN<double, double>(__VA_ARGS__);               \
+    case IBLB_FP16: return FN<float, __half>(__VA_ARGS__);                \
+    case IBLB_BF16: return FN<float, __nv_bfloat16>(__VA_ARGS__);         \
+    default: return FN<float, float>(__VA_ARGS__);                        \
+  }
+
+cudaError_t launch_stream_collide(Ctx &c, int first, cudaStream_t s) {
+  IBLB_DISPATCH(c, stream_collide_t, c, first, s)
+}
+
+cudaError_t launch_stream_collide_tiles(Ctx &c, int first, cudaStream_t s) {
+  IBLB_DISPATCH(c, stream_collide_tiles_t, c, first, s)
+}
+
+cudaError_t launch_shell_velocity(Ctx &c, cudaStream_t s) { IBLB_DISPATCH(c, shell_velocity_t, c, s) }
+
+cudaError_t launch_fields(Ctx &c, double *rho_dev, double *u_dev) {
+  IBLB_DISPATCH(c, fields_t, c, rho_dev, u_dev)
+}
+
+cudaError_t launch_populations(Ctx &c, double *f_dev) { IBLB_DISPATCH(c, populations_t, c, f_dev) }
 
 cudaError_t launch_init_equilibrium(Ctx &c, const double *rho_dev, const double *u_dev) {
-  const int blocks = (int)((c.ncell + 255) / 256);
-  if (c.precision == IBLB_FP64)
-    init_equilibrium_kernel<double><<<blocks, 256, 0, c.stream>>>(
-        (double *)c.f[c.cur], lat_params<double>(c), c.rho0, rho_dev, u_dev);
-  else
-    init_equilibrium_kernel<float><<<blocks, 256, 0, c.stream>>>(
-        (float *)c.f[c.cur], lat_params<float>(c), c.rho0, rho_dev, u_dev);
-  return cudaGetLastError();
+  IBLB_DISPATCH(c, init_equilibrium_t, c, rho_dev, u_dev)
 }
 
 }  // namespace iblb
