@@ -251,6 +251,45 @@ def time_variant(wl, precision, steps, warmup):
             "interface_sms": sms}
 
 
+def time_ensemble(steps, warmup, n=96, seed=2305):
+    """The batched-ensemble workload: n independent wetting boxes of uneven sizes (edges from
+    {48, 64, 80, 96}), advanced together by iblb_batch_step (one CUDA graph launch per two
+    steps) after iblb_batch_tune, against the same boxes stepped one after another."""
+    import torch
+    from paper_2305_18919_gb300 import binding
+    wls = inputs.wetting_ensemble(n, seed)
+    cells = sum(w.cells for w in wls)
+    fluid = sum(w.nx * w.ny * (w.nz - 2) for w in wls)
+    b = binding.Batch.from_workloads(wls)
+    rows = b.tune(trials=3)
+    b.step(max(4, warmup))
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    b.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    # the same instances, one context after another (each iblb_step(steps) on its own stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for lat in b.contexts:
+        lat.step(steps)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    b.close()
+    peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    return {"workload": f"wetting_ensemble_{n}_seed{seed}", "instances": n, "nodes": cells,
+            "value": round(replica_mlups(1, cells, steps, ms * 1e-3), 1), "unit": "MLUPS",
+            "ms_per_step": round(ms / steps, 4), "steps": steps,
+            "step_frac": round(152 * fluid / (ms / steps * 1e-3) / 1e9 / peak, 4),
+            "sequential_value": round(replica_mlups(1, cells, steps, seq_s), 1),
+            "k1_rows_chosen": {str(r): rows.count(r) for r in sorted(set(rows))},
+            "path": "iblb_batch_step (graph of two steps of every instance), FP32"}
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     from paper_2305_18919_gb300 import binding
@@ -354,6 +393,8 @@ def run_gpu(args, wl, rank, world):
     }
     if variants:
         line["precision_variants"] = variants
+    if rank == 0 and world == 1 and args.ensemble_steps > 0 and wl.name.startswith("shear256"):
+        line["ensemble"] = time_ensemble(args.ensemble_steps, 10)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -367,6 +408,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="shear256")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ensemble-steps", type=int, default=200,
+                    help="steps timed for the 96-box batched ensemble reported beside the "
+                         "headline (0: skip)")
     ap.add_argument("--variant-steps", type=int, default=1000,
                     help="steps timed for each 16-bit storage variant reported beside the FP32 "
                          "headline (0: skip)")

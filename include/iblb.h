@@ -179,6 +179,44 @@ int iblb_profile(iblb_ctx *ctx, double *k1_ms, int64_t *k1_launches, int64_t *ke
 int iblb_mesh_volume_noalloc(const double *q_dev, const int32_t *faces_dev, int32_t nf,
                              const double *centre, double *V_dev, void *cuda_stream);
 
+/* ---- Batched ensemble ----------------------------------------------------------------------
+   Many independent contexts (lattices and meshes of any sizes) advanced together. The paper
+   runs one box at a time; this is the ensemble form of its parameter sweeps (Sec. V), a library
+   service with no counterpart in the paper.
+
+   iblb_batch_create makes n contexts, instance i from descs[i] (ib_sms is ignored: the
+   instances share all SMs), each with its own CUDA stream, and returns the batch in *out. The
+   contexts are configured and read through the single-context calls on the handles that
+   iblb_batch_context returns (borrowed: they stay owned by the batch and are released by
+   iblb_batch_destroy, which synchronises). `cuda_stream` (a cudaStream_t, NULL: legacy default
+   stream) orders the batch against the caller's work.
+
+   iblb_batch_step advances every instance by nsteps coupled steps (the iblb_step sequence).
+   It records two steps of every instance in one CUDA graph, at its first use and again after
+   any instance was reconfigured (mesh, interface parameters, initial state, tuning) or stepped
+   alone by an odd count, and replays that graph: one graph launch per two steps for the whole
+   ensemble. A freshly initialised instance takes its first step outside the graph. The call
+   synchronises once at its end and reads every instance's health word: it returns the first
+   failing instance's IBLB_EUNSTABLE / IBLB_ECAPACITY (message in iblb_batch_last_error) and
+   iblb_batch_status fills status[n] with each instance's result. Results are identical, bit
+   for bit, to stepping each context alone without an SM partition.
+
+   iblb_batch_tune picks, per distinct lattice shape and precision, the lattice rows per block
+   (1, 2 or 4, within 128 threads) of the stream-collide pass by timing `trials` launches of
+   each on the instance's own stream (the state is not advanced); iblb_batch_k1_rows reports
+   the choice. */
+typedef struct iblb_batch iblb_batch;
+int iblb_batch_create(const iblb_lattice_desc *descs, int32_t n, void *cuda_stream,
+                      iblb_batch **out);
+void iblb_batch_destroy(iblb_batch *batch);
+const char *iblb_batch_last_error(const iblb_batch *batch);
+int32_t iblb_batch_size(const iblb_batch *batch);
+iblb_ctx *iblb_batch_context(iblb_batch *batch, int32_t i); /* NULL if i is out of range */
+int iblb_batch_tune(iblb_batch *batch, int32_t trials);
+int32_t iblb_batch_k1_rows(const iblb_batch *batch, int32_t i);
+int iblb_batch_step(iblb_batch *batch, int32_t nsteps);
+int iblb_batch_status(const iblb_batch *batch, int32_t *status);
+
 /* SMs of the interface partition of iblb_step (0: no partition, -1: NULL context). */
 int32_t iblb_interface_sms(const iblb_ctx *ctx);
 

@@ -82,6 +82,15 @@ SIGNATURES = {
     "iblb_bytes_per_cell": (_i64, [_vp]),
     "iblb_interface_sms": (_i32, [_vp]),
     "iblb_mesh_volume_noalloc": (_i32, [_vp, _vp, _i32, _dp, _vp, _vp]),
+    "iblb_batch_create": (_i32, [ctypes.POINTER(iblb_lattice_desc), _i32, _vp, ctypes.POINTER(_vp)]),
+    "iblb_batch_destroy": (None, [_vp]),
+    "iblb_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "iblb_batch_size": (_i32, [_vp]),
+    "iblb_batch_context": (_vp, [_vp, _i32]),
+    "iblb_batch_tune": (_i32, [_vp, _i32]),
+    "iblb_batch_k1_rows": (_i32, [_vp, _i32]),
+    "iblb_batch_step": (_i32, [_vp, _i32]),
+    "iblb_batch_status": (_i32, [_vp, _ip]),
 }
 
 
@@ -137,26 +146,44 @@ def mesh_volume_noalloc(q_dev_ptr: int, faces_dev_ptr: int, nf: int, centre, V_d
                                               ctypes.c_void_p(V_dev_ptr), s))
 
 
+def lattice_desc(nx, ny, nz, tau, rho0=1.0, wall_u_bottom=(0, 0, 0), wall_u_top=(0, 0, 0),
+                 body_force=(0, 0, 0), precision="fp32", z_periodic=False, ib_sms=0):
+    """An iblb_lattice_desc filled from Python values."""
+    d = iblb_lattice_desc()
+    d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+    d.precision = _PRECISION[precision] if isinstance(precision, str) else int(precision)
+    d.z_periodic = int(bool(z_periodic))
+    d.ib_sms = int(ib_sms)
+    d.tau, d.rho0 = float(tau), float(rho0)
+    d.wall_u_bottom[:] = [float(v) for v in wall_u_bottom]
+    d.wall_u_top[:] = [float(v) for v in wall_u_top]
+    d.body_force[:] = [float(v) for v in body_force]
+    return d
+
+
+def workload_desc(wl, precision=None, ib_sms=0):
+    """The lattice description of a workload (inputs.Workload)."""
+    return lattice_desc(wl.nx, wl.ny, wl.nz, wl.tau, 1.0, wl.wall_u_bottom, wl.wall_u_top,
+                        wl.body_force, precision or wl.precision, False, ib_sms)
+
+
 class Lattice:
     """One IB-LB context (lattice + optional interface mesh) on the current CUDA device."""
 
     def __init__(self, nx, ny, nz, tau, rho0=1.0, wall_u_bottom=(0, 0, 0), wall_u_top=(0, 0, 0),
                  body_force=(0, 0, 0), precision="fp32", z_periodic=False, stream=None,
-                 ib_sms=0):
+                 ib_sms=0, _handle=None):
         self._L = lib()
-        d = iblb_lattice_desc()
-        d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
-        d.precision = _PRECISION[precision] if isinstance(precision, str) else int(precision)
-        d.z_periodic = int(bool(z_periodic))
-        d.ib_sms = int(ib_sms)
-        d.tau, d.rho0 = float(tau), float(rho0)
-        d.wall_u_bottom[:] = [float(v) for v in wall_u_bottom]
-        d.wall_u_top[:] = [float(v) for v in wall_u_top]
-        d.body_force[:] = [float(v) for v in body_force]
         self.shape = (int(nx), int(ny), int(nz))
         self.precision = precision
         self.nv = 0
         self.nf = 0
+        self._owned = _handle is None
+        if _handle is not None:  # a context owned by a Batch
+            self.h = ctypes.c_void_p(_handle)
+            return
+        d = lattice_desc(nx, ny, nz, tau, rho0, wall_u_bottom, wall_u_top, body_force, precision,
+                         z_periodic, ib_sms)
         self.h = ctypes.c_void_p()
         s = stream if stream is not None else _current_stream()
         rc = self._L.iblb_create(ctypes.byref(d), s, ctypes.byref(self.h))
@@ -178,9 +205,9 @@ class Lattice:
             raise IBLBError(rc, msg.decode() if msg else "")
 
     def close(self):
-        if self.h:
+        if self.h and self._owned:
             self._L.iblb_destroy(self.h)
-            self.h = ctypes.c_void_p()
+        self.h = ctypes.c_void_p()
 
     def __del__(self):
         try:
@@ -295,3 +322,65 @@ class Lattice:
 
     def bytes_per_cell(self) -> int:
         return int(self._L.iblb_bytes_per_cell(self.h))
+
+
+class Batch:
+    """Independent contexts advanced together (iblb_batch_*): one CUDA graph launch per two
+    steps for the whole ensemble. `contexts` are Lattice views of the batch's contexts."""
+
+    def __init__(self, descs, stream=None):
+        self._L = lib()
+        arr = (iblb_lattice_desc * len(descs))(*descs)
+        self.h = ctypes.c_void_p()
+        s = stream if stream is not None else _current_stream()
+        rc = self._L.iblb_batch_create(arr, len(descs), s, ctypes.byref(self.h))
+        if rc != IBLB_OK:
+            raise IBLBError(rc, "iblb_batch_create failed")
+        names = {v: k for k, v in _PRECISION.items()}
+        self.contexts = []
+        for i, d in enumerate(descs):
+            h = self._L.iblb_batch_context(self.h, i)
+            self.contexts.append(Lattice(d.nx, d.ny, d.nz, d.tau, precision=names[d.precision],
+                                         _handle=h))
+
+    @classmethod
+    def from_workloads(cls, workloads, precision=None, stream=None):
+        b = cls([workload_desc(wl, precision) for wl in workloads], stream)
+        for lat, wl in zip(b.contexts, workloads):
+            v, f = wl.mesh()
+            lat.add_mesh(v, f)
+            lat.set_interface(wl.alpha, wl.kV, wl.eps, wl.xi, wl.wall_force_on, wl.volume_force_on)
+        return b
+
+    def __len__(self):
+        return len(self.contexts)
+
+    def _check(self, rc):
+        if rc != IBLB_OK:
+            msg = self._L.iblb_batch_last_error(self.h)
+            raise IBLBError(rc, msg.decode() if msg else "")
+
+    def step(self, nsteps=1):
+        self._check(self._L.iblb_batch_step(self.h, int(nsteps)))
+
+    def tune(self, trials=5):
+        self._check(self._L.iblb_batch_tune(self.h, int(trials)))
+        return [int(self._L.iblb_batch_k1_rows(self.h, i)) for i in range(len(self))]
+
+    def status(self):
+        out = np.zeros(len(self), dtype=np.int32)
+        self._check(self._L.iblb_batch_status(self.h, out.ctypes.data_as(_ip)))
+        return out
+
+    def close(self):
+        if self.h:
+            for lat in self.contexts:
+                lat.h = ctypes.c_void_p()
+            self._L.iblb_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

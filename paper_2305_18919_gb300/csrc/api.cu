@@ -15,10 +15,6 @@
 
 using iblb::Ctx;
 
-struct iblb_ctx {
-  Ctx c;
-};
-
 namespace {
 
 int fail(Ctx &c, int code, const std::string &msg) {
@@ -84,13 +80,17 @@ int read_health(Ctx &c, int *h) {
   return 0;
 }
 
+// An unstable run reports that first: its garbage positions can also leave tiles unmarked.
 int health_error(Ctx &c, int h) {
-  if (h & iblb::H_CAPACITY) return fail(c, IBLB_ECAPACITY, "active-tile table capacity exceeded");
+  const int unstable = iblb::H_NAN | iblb::H_FAST | iblb::H_WALL | iblb::H_VOLUME;
+  if (!(h & unstable))
+    return fail(c, IBLB_ECAPACITY, "active-tile table capacity exceeded");
   std::string m = "health check failed:";
   if (h & iblb::H_NAN) m += " NaN in vertex velocity;";
   if (h & iblb::H_FAST) m += " |qdot| >= 0.1;";
   if (h & iblb::H_WALL) m += " vertex within 0.05 of a wall plane;";
   if (h & iblb::H_VOLUME) m += " |V/V0 - 1| > 0.05;";
+  if (h & iblb::H_CAPACITY) m += " (active-tile table capacity also exceeded);";
   return fail(c, IBLB_EUNSTABLE, m);
 }
 
@@ -439,6 +439,7 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
   CUDA_TRY(c, cudaMemcpyAsync(c.vf_list, vf_list.data(), (size_t)3 * nf * sizeof(int), cudaMemcpyHostToDevice, c.stream));
   if (int rc = upload_reference(c, verts, fref, fgeo)) return rc;
   c.map = 0;
+  c.config_gen++;
   c.have_force = 0;
   int rc = remark(c, 0);
   if (rc) return rc;
@@ -456,6 +457,7 @@ int iblb_set_interface(iblb_ctx *h, int32_t mesh_id, const iblb_iface_params *p)
   if (!std::isfinite(p->kV) || !std::isfinite(p->eps) || !(p->xi > 0))
     return fail(c, IBLB_EINVAL, "invalid kV, eps or xi");
   c.iface = *p;
+  c.config_gen++;
   return IBLB_OK;
 }
 
@@ -478,6 +480,7 @@ int iblb_init_equilibrium(iblb_ctx *h, const double *rho, const double *u) {
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
   c.fresh = 1;
   c.have_force = 0;
+  c.config_gen++;
   return IBLB_OK;
 }
 
@@ -493,7 +496,19 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
   if (nsteps < 0) return fail(c, IBLB_EINVAL, "nsteps < 0");
   if (nsteps == 0) return IBLB_OK;
   CUDA_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
-  // the library streams start after everything queued so far on the caller's stream
+  if (int rc = iblb::enqueue_steps(c, nsteps)) return rc;
+  int hw = 0;
+  if (int rc = read_health(c, &hw)) return rc;
+  if (hw) return health_error(c, hw);
+  return IBLB_OK;
+}
+
+}  // extern "C"
+
+namespace iblb {
+
+int enqueue_steps(Ctx &c, int nsteps) {
+  // the library streams start after everything queued so far on the context's stream
   CUDA_TRY(c, cudaEventRecord(c.ev_sync, c.stream));
   CUDA_TRY(c, cudaStreamWaitEvent(c.ib, c.ev_sync, 0));
   if (c.ls != c.stream) CUDA_TRY(c, cudaStreamWaitEvent(c.ls, c.ev_sync, 0));
@@ -503,7 +518,7 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
       CUDA_TRY(c, iblb::launch_vertex_forces(c, 2, c.ib));
       CUDA_TRY(c, iblb::launch_spread(c, c.ib));
       CUDA_TRY(c, cudaEventRecord(c.ev_force, c.ib));
-      c.kernel_launches += 3;
+      c.kernel_launches += 4;  // face, vertex and the two spreading passes
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c.profiling) {
@@ -534,18 +549,21 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
     }
     c.steps_done++;
   }
-  // the caller's stream continues after the last step on both library streams
+  // the context's stream continues after the last step on both library streams
   CUDA_TRY(c, cudaEventRecord(c.ev_sync, c.ib));
   CUDA_TRY(c, cudaStreamWaitEvent(c.stream, c.ev_sync, 0));
   if (c.ls != c.stream) {
     CUDA_TRY(c, cudaEventRecord(c.ev_coll, c.ls));
     CUDA_TRY(c, cudaStreamWaitEvent(c.stream, c.ev_coll, 0));
   }
-  int hw = 0;
-  if (int rc = read_health(c, &hw)) return rc;
-  if (hw) return health_error(c, hw);
-  return IBLB_OK;
+  return 0;
 }
+
+int health_status(Ctx &c, int hw) { return hw ? health_error(c, hw) : IBLB_OK; }
+
+}  // namespace iblb
+
+extern "C" {
 
 int iblb_read_fields(iblb_ctx *h, double *rho, double *u) {
   if (!h || !rho || !u) return IBLB_EINVAL;
@@ -746,6 +764,7 @@ int iblb_load_state(iblb_ctx *h, const char *path) {
     CUDA_TRY(c, cudaMemcpyAsync(c.qdot, qdbuf.data(), qdbuf.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
     c.have_force = 0;
     if (int rc = remark(c, c.map)) return rc;
+    c.config_gen++;
   }
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
   return IBLB_OK;

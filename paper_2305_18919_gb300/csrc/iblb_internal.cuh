@@ -128,8 +128,18 @@ struct Ctx {
   double *dscratch = nullptr;  // host-transfer staging buffer (doubles)
   size_t dscratch_len = 0;
   int sm_count = 0;
+  int k1_rows = 0;          // lattice rows per block of the stream-collide pass (0: 1)
+  uint64_t config_gen = 0;  // bumped by every call that changes what a queued step launches
   std::string err;
 };
+
+// Queue nsteps coupled steps on the context's streams: no synchronisation, no health read
+// (iblb_step adds those). Returns 0 or an IBLB_E* code (message in c.err).
+int enqueue_steps(Ctx &c, int nsteps);
+// IBLB_OK for a clear health word, else the matching error code (message in c.err).
+int health_status(Ctx &c, int health_word);
+// Lattice rows per block of the stream-collide pass (k1_rows within the launch bound).
+int k1_block_rows(const Ctx &c);
 
 // Launchers (each returns cudaGetLastError() of its launch) on stream `s`.
 // Stream-collide of every fluid node with the body force only (no interface force).
@@ -154,3 +164,8 @@ cudaError_t launch_phi_to_double(Ctx &c, double *phi_dev);
 cudaError_t launch_volume(Ctx &c, double *V_dev);
 
 }  // namespace iblb
+
+// The opaque handle of the C ABI.
+struct iblb_ctx {
+  iblb::Ctx c;
+};

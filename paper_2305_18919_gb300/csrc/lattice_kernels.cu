@@ -323,12 +323,14 @@ __device__ __forceinline__ void store_pair(S *__restrict__ fout, const LatParams
 // their interface force, so this pass does not wait for the interface chain of the step.
 // Each thread owns the two nodes (x0, x0 + 1), x0 even: populations that do not move along x
 // and every store are one aligned 2-wide access, and the address arithmetic is shared.
-template <typename real, typename S, bool FIRST, bool FORCE>
+// With ROWS each block covers blockDim.y lattice rows (small lattices); without, one row
+// (kept as its own instance: the row arithmetic costs the single-row kernel registers).
+template <typename real, typename S, bool FIRST, bool FORCE, bool ROWS>
 __global__ void __launch_bounds__(128) stream_collide_kernel(const S *__restrict__ fin,
                                                              S *__restrict__ fout,
                                                              const LatParams<real> P, int z0) {
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y;
+  const int y = ROWS ? blockIdx.y * blockDim.y + threadIdx.y : blockIdx.y;
   const int z = blockIdx.z + z0;
   if (x0 >= P.nx) return;
   real a[Q], b[Q];  // populations of nodes x0 and x0 + 1
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(128) stream_collide_quad_kernel(const S *__res
                                                                   int z0) {
   using V2 = typename Storage<S>::V2;
   const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;  // blockDim.y rows per block
   const int z = blockIdx.z + z0;
   if (x0 >= P.nx) return;
   const size_t plane = (size_t)P.nx * P.ny;
@@ -704,16 +706,17 @@ cudaError_t stream_collide_quad_t(Ctx &c, int first, cudaStream_t st) {
   const int nzf = c.has_walls ? c.nz - 2 : c.nz;
   const int quads = c.nx / 4;  // four nodes per thread along x
   const int bx = quads < 128 ? quads : 128;
-  dim3 grid((quads + bx - 1) / bx, c.ny, nzf);
+  const int rows = k1_block_rows(c);
+  const dim3 grid((quads + bx - 1) / bx, c.ny / rows, nzf), block(bx, rows);
   const S *fin = (const S *)c.f[c.cur];
   S *fout = (S *)c.f[c.cur ^ 1];
   const bool force = c.g[0] != 0.0 || c.g[1] != 0.0 || c.g[2] != 0.0;
   if (first) {
-    if (force) stream_collide_quad_kernel<S, true, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
-    else stream_collide_quad_kernel<S, true, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    if (force) stream_collide_quad_kernel<S, true, true><<<grid, block, 0, st>>>(fin, fout, P, z0);
+    else stream_collide_quad_kernel<S, true, false><<<grid, block, 0, st>>>(fin, fout, P, z0);
   } else {
-    if (force) stream_collide_quad_kernel<S, false, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
-    else stream_collide_quad_kernel<S, false, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    if (force) stream_collide_quad_kernel<S, false, true><<<grid, block, 0, st>>>(fin, fout, P, z0);
+    else stream_collide_quad_kernel<S, false, false><<<grid, block, 0, st>>>(fin, fout, P, z0);
   }
   return cudaGetLastError();
 }
@@ -726,16 +729,27 @@ cudaError_t stream_collide_t(Ctx &c, int first, cudaStream_t st) {
   const int nzf = c.has_walls ? c.nz - 2 : c.nz;
   const int half = c.nx / 2;  // two nodes per thread along x
   const int bx = half < 128 ? half : 128;
-  dim3 grid((half + bx - 1) / bx, c.ny, nzf);
+  const int rows = k1_block_rows(c);
+  const dim3 grid((half + bx - 1) / bx, c.ny / rows, nzf), block(bx, rows);
   const S *fin = (const S *)c.f[c.cur];
   S *fout = (S *)c.f[c.cur ^ 1];
   const bool force = c.g[0] != 0.0 || c.g[1] != 0.0 || c.g[2] != 0.0;
-  if (first) {
-    if (force) stream_collide_kernel<real, S, true, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
-    else stream_collide_kernel<real, S, true, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+  if (rows > 1) {
+    if (first) {
+      if (force) stream_collide_kernel<real, S, true, true, true><<<grid, block, 0, st>>>(fin, fout, P, z0);
+      else stream_collide_kernel<real, S, true, false, true><<<grid, block, 0, st>>>(fin, fout, P, z0);
+    } else {
+      if (force) stream_collide_kernel<real, S, false, true, true><<<grid, block, 0, st>>>(fin, fout, P, z0);
+      else stream_collide_kernel<real, S, false, false, true><<<grid, block, 0, st>>>(fin, fout, P, z0);
+    }
   } else {
-    if (force) stream_collide_kernel<real, S, false, true><<<grid, bx, 0, st>>>(fin, fout, P, z0);
-    else stream_collide_kernel<real, S, false, false><<<grid, bx, 0, st>>>(fin, fout, P, z0);
+    if (first) {
+      if (force) stream_collide_kernel<real, S, true, true, false><<<grid, block, 0, st>>>(fin, fout, P, z0);
+      else stream_collide_kernel<real, S, true, false, false><<<grid, block, 0, st>>>(fin, fout, P, z0);
+    } else {
+      if (force) stream_collide_kernel<real, S, false, true, false><<<grid, block, 0, st>>>(fin, fout, P, z0);
+      else stream_collide_kernel<real, S, false, false, false><<<grid, block, 0, st>>>(fin, fout, P, z0);
+    }
   }
   return cudaGetLastError();
 }
@@ -802,6 +816,16 @@ cudaError_t init_equilibrium_t(Ctx &c, const double *rho_dev, const double *u_de
 }
 
 }  // namespace
+
+int k1_block_rows(const Ctx &c) {
+  // a block is at most 128 threads (the kernels' launch bound); ny is a multiple of 4, so
+  // every row count 1, 2, 4 divides it
+  const int per_row = c.pop_size == 2 ? c.nx / 4 : c.nx / 2;
+  const int bx = per_row < 128 ? per_row : 128;
+  int rows = c.k1_rows > 0 ? c.k1_rows : 1;
+  while (rows > 1 && bx * rows > 128) rows /= 2;
+  return rows;
+}
 
 // Dispatch on the context's precision: (arithmetic, storage) = (double, double) for FP64,
 // (float, float) for FP32, (float, half) for FP16 and (float, bfloat16) for BF16.

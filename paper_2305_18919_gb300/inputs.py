@@ -181,6 +181,40 @@ def shear_256_fp32_box(n: int = 128, seed: int = 2305) -> Workload:
     return wl
 
 
+def wetting_ensemble(n: int = 96, seed: int = 2305, edges=(48, 64, 80, 96),
+                     eps_scale: float = 0.1) -> list:
+    """Independent static-wetting boxes of uneven sizes (the batched-ensemble workload).
+
+    Per instance, from the seed: lattice edges drawn per axis from `edges`; R = 0.3 x the
+    smallest edge; icosphere subdivision 3 if R < 16, 4 if R < 24, else 5; alpha class drawn
+    from the pure droplet, softly coated and rigidly coated classes (Table I) times
+    alpha_bar ~ U[0.005, 0.05]; wall strength eps = r * eps_scale * alpha_bar with r ~ U[0, 1].
+    Walls at z = 0 and the top layer, FP32, the particle centred in x, y and placed at the LJ
+    minimum above the bottom wall. With eps_scale = 1 the strongest walls pull the fine meshes
+    through the wall within a few steps (the FP64 oracle diverges as well: the wall force acts
+    per face, Eq. 19), so the default keeps eps / alpha_bar in [0, 0.1].
+    """
+    rng = np.random.default_rng(seed)
+    classes = [ALPHA_CLASSES[k] for k in ("droplet", "softly_coated", "rigidly_coated")]
+    out = []
+    for i in range(n):
+        nx, ny, nz = (int(e) for e in rng.choice(edges, size=3))
+        r = 0.3 * min(nx, ny, nz)
+        sub = 3 if r < 16 else (4 if r < 24 else 5)
+        cls = classes[int(rng.integers(3))]
+        abar = float(rng.uniform(0.005, 0.05))
+        ratio = float(rng.uniform(0.0, 1.0)) * eps_scale
+        zc = 0.5 + r + 2.0 ** (1.0 / 6.0) * LJ_XI
+        out.append(Workload(
+            name=f"ensemble{i}_{nx}x{ny}x{nz}_sub{sub}", nx=nx, ny=ny, nz=nz, tau=1.0,
+            wall_u_bottom=(0.0, 0.0, 0.0), wall_u_top=(0.0, 0.0, 0.0),
+            subdivisions=sub, radius=r, centre=(nx / 2, ny / 2, zc),
+            alpha=tuple(abar * a for a in cls), eps=ratio * abar, wall_force_on=1,
+            volume_force_on=1, steps=10000, precision="fp32",
+            extra={"alpha_bar": abar, "eps_over_alpha": ratio}))
+    return out
+
+
 def scaled_shear(n: int, subdivisions: int, radius: float, tau: float = 1.0,
                  wall_u: float = 0.01, alpha=(0.01, 0.0, 0.0), precision: str = "fp32",
                  nx: int | None = None, ny: int | None = None) -> Workload:
