@@ -217,6 +217,27 @@ int32_t iblb_batch_k1_rows(const iblb_batch *batch, int32_t i);
 int iblb_batch_step(iblb_batch *batch, int32_t nsteps);
 int iblb_batch_status(const iblb_batch *batch, int32_t *status);
 
+/* ---- Adjoint: gradients of an observable of the final vertex positions ----------------------
+   The discrete adjoint of the coupled step (Sec. III) with respect to the interface parameters
+   theta = (alpha1, alpha2, alpha3, eps) of Eq. 2 and Eq. 19; IBLB_FP64 contexts with a mesh.
+
+   iblb_adjoint_record advances nsteps steps from the current state (as iblb_step would) and keeps
+   a copy of the state (populations and positions) every `every` steps on the device: memory
+   ceil(nsteps/every) + 1 copies of the state. The context is left at the end of the run.
+
+   iblb_adjoint_gradient takes dJdq (host [nv][3]: the derivative of an observable J with respect
+   to the final positions) and writes dJdtheta (host [4]). It runs the recorded steps backwards:
+   each segment is recomputed forward from its copy (every + 1 more states on the device), then
+   the transposed step is applied state by state. The context is returned to the end of the run;
+   the recording stays valid for further calls with other dJdq.
+
+   iblb_adjoint_release frees the recording and the work arrays (iblb_destroy also does).
+   Errors: IBLB_EINVAL (not FP64, no mesh, nothing recorded, nsteps or every < 1), the health
+   errors of iblb_step during the record or the recomputation, IBLB_ENOMEM, IBLB_ECUDA. */
+int iblb_adjoint_record(iblb_ctx *ctx, int32_t nsteps, int32_t every);
+int iblb_adjoint_gradient(iblb_ctx *ctx, const double *dJdq, double *dJdtheta);
+int iblb_adjoint_release(iblb_ctx *ctx);
+
 /* SMs of the interface partition of iblb_step (0: no partition, -1: NULL context). */
 int32_t iblb_interface_sms(const iblb_ctx *ctx);
 

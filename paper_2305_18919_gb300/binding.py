@@ -91,6 +91,9 @@ SIGNATURES = {
     "iblb_batch_k1_rows": (_i32, [_vp, _i32]),
     "iblb_batch_step": (_i32, [_vp, _i32]),
     "iblb_batch_status": (_i32, [_vp, _ip]),
+    "iblb_adjoint_record": (_i32, [_vp, _i32, _i32]),
+    "iblb_adjoint_gradient": (_i32, [_vp, _dp, _dp]),
+    "iblb_adjoint_release": (_i32, [_vp]),
 }
 
 
@@ -319,6 +322,21 @@ class Lattice:
 
     def interface_sms(self) -> int:
         return int(self._L.iblb_interface_sms(self.h))
+
+    # --- adjoint ---------------------------------------------------------------------
+    def adjoint_record(self, nsteps, every=100):
+        """Advance nsteps steps keeping a state copy every `every` steps (iblb_adjoint_record)."""
+        self._check(self._L.iblb_adjoint_record(self.h, int(nsteps), int(every)))
+
+    def adjoint_gradient(self, dJdq):
+        """dJ/d(alpha1, alpha2, alpha3, eps) from dJ/dq at the end of the recorded run."""
+        g = _f64(dJdq, (self.nv, 3))
+        out = np.zeros(4)
+        self._check(self._L.iblb_adjoint_gradient(self.h, _dptr(g), _dptr(out)))
+        return out
+
+    def adjoint_release(self):
+        self._check(self._L.iblb_adjoint_release(self.h))
 
     def bytes_per_cell(self) -> int:
         return int(self._L.iblb_bytes_per_cell(self.h))

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libiblb.so")
-SOURCES = ["api.cu", "lattice_kernels.cu", "ib_kernels.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "lattice_kernels.cu", "ib_kernels.cu", "noalloc.cu", "batch.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"] + ARCH

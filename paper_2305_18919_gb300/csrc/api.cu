@@ -335,6 +335,7 @@ void iblb_destroy(iblb_ctx *h) {
   dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.xref); dfree(c.fgeo); dfree(c.disp); dfree(c.vf_start); dfree(c.vf_list);
   dfree(c.fcontrib); dfree(c.fnorm); dfree(c.vol_partial); dfree(c.phi); dfree(c.gvol); dfree(c.stencil);
   dfree(c.dscratch);
+  iblb::adjoint_free(c);
   for (cudaEvent_t ev : c.ev_pool) cudaEventDestroy(ev);
   for (cudaEvent_t ev : c.ev_near) cudaEventDestroy(ev);
   if (c.ev_force) cudaEventDestroy(c.ev_force);
@@ -560,6 +561,15 @@ int enqueue_steps(Ctx &c, int nsteps) {
 }
 
 int health_status(Ctx &c, int hw) { return hw ? health_error(c, hw) : IBLB_OK; }
+
+int restore_state(Ctx &c, const void *P, const double *q, int fresh) {
+  CUDA_TRY(c, cudaMemcpyAsync(c.f[c.cur], P, (size_t)Q * c.ncell * c.pop_size,
+                              cudaMemcpyDeviceToDevice, c.stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c.q, q, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                              c.stream));
+  c.fresh = fresh;
+  return remark(c, c.map);
+}
 
 }  // namespace iblb
 

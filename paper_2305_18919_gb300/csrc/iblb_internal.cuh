@@ -126,6 +126,7 @@ struct Ctx {
   std::vector<cudaEvent_t> ev_near;  // events around the active-tile collision (profiling)
   size_t ev_near_used = 0;
   double *dscratch = nullptr;  // host-transfer staging buffer (doubles)
+  void *adj = nullptr;         // recorded trajectory and work arrays of the adjoint (adjoint.cu)
   size_t dscratch_len = 0;
   int sm_count = 0;
   int k1_rows = 0;          // lattice rows per block of the stream-collide pass (0: 1)
@@ -138,6 +139,12 @@ struct Ctx {
 int enqueue_steps(Ctx &c, int nsteps);
 // IBLB_OK for a clear health word, else the matching error code (message in c.err).
 int health_status(Ctx &c, int health_word);
+// Replace the state by populations P (the storage layout of f[cur]) and positions q (device
+// arrays), with the given fresh flag, and mark the tiles of q: the next step continues from
+// there exactly as from the state that P and q were copied from.
+int restore_state(Ctx &c, const void *P, const double *q, int fresh);
+// Release the adjoint's memory (no-op without one).
+void adjoint_free(Ctx &c);
 // Lattice rows per block of the stream-collide pass (k1_rows within the launch bound).
 int k1_block_rows(const Ctx &c);
 

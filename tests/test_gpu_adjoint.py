@@ -1,0 +1,94 @@
+"""The discrete adjoint on the GPU (iblb_adjoint_*, FP64) against the reference gradients of
+oracle/adjoint.py (the oracle's step restated in float64 PyTorch and differentiated by
+autograd, itself pinned to finite differences of the C oracle), and against central finite
+differences of the GPU's own forward runs on a larger box."""
+import copy
+
+import numpy as np
+import pytest
+
+from paper_2305_18919_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def objective(q):
+    c = q.mean(0)
+    return ((q[:, 2] - c[2]) ** 2).mean() + 0.3 * ((q[:, 0] - c[0]) ** 2).mean() + c[2]
+
+
+def objective_grad(q):
+    qt = torch.tensor(q, dtype=torch.float64, requires_grad=True)
+    (g,) = torch.autograd.grad(objective(qt), qt)
+    return g.numpy()
+
+
+def _small():
+    wl = inputs.scaled_wetting(16, 14, 2, 4.0, alpha=(2e-3, 1e-3, 2e-3), eps=1e-3,
+                               precision="fp64")
+    wl.wall_u_bottom = (-0.005, 0.002, 0.0)
+    wl.wall_u_top = (0.004, 0.0, 0.0)
+    return wl
+
+
+def _gpu_gradient(wl, nsteps, every):
+    from paper_2305_18919_gb300 import binding
+    lat = binding.Lattice.from_workload(wl, precision="fp64")
+    lat.adjoint_record(nsteps, every)
+    q = lat.vertices()
+    g = lat.adjoint_gradient(objective_grad(q))
+    q_after = lat.vertices()
+    lat.close()
+    return g, q, q_after
+
+
+@pytest.mark.parametrize("every", [30, 7, 1])
+def test_gpu_adjoint_equals_reference_gradients(every):
+    from oracle import adjoint as oa
+    wl = _small()
+    _, g_ref, q_ref = oa.gradient(wl, 30, objective)
+    g, q, q_after = _gpu_gradient(wl, 30, every)
+    assert np.abs(q - q_ref).max() < 1e-11           # the same trajectory
+    assert np.array_equal(q_after, q)                # the context is back at the end
+    np.testing.assert_allclose(g, g_ref, rtol=1e-7, atol=1e-12 * np.abs(g_ref).max())
+
+
+def test_gpu_adjoint_equals_finite_differences_of_gpu_runs():
+    from paper_2305_18919_gb300 import binding
+    wl = inputs.scaled_wetting(32, 24, 3, 6.0, alpha=(4e-3, 2e-3, 1e-3), eps=5e-4,
+                               precision="fp64")
+    N = 120
+    g, _, _ = _gpu_gradient(wl, N, 40)
+
+    def J(params):
+        w = copy.deepcopy(wl)
+        w.alpha, w.eps = tuple(params[:3]), params[3]
+        lat = binding.Lattice.from_workload(w, precision="fp64")
+        lat.step(N)
+        q = lat.vertices()
+        lat.close()
+        return float(objective(q))
+
+    p0 = np.array(list(wl.alpha) + [wl.eps])
+    for k in range(4):
+        h = 1e-3 * p0[k]
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (J(pp) - J(pm)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-5 * abs(fd)
+
+
+def test_adjoint_rejects_what_it_cannot_do():
+    from paper_2305_18919_gb300 import binding
+    wl = _small()
+    lat = binding.Lattice.from_workload(wl, precision="fp32")
+    with pytest.raises(binding.IBLBError) as e:
+        lat.adjoint_record(5, 5)
+    assert e.value.code == binding.IBLB_EINVAL
+    lat.close()
+    lat = binding.Lattice.from_workload(wl, precision="fp64")
+    with pytest.raises(binding.IBLBError):
+        lat.adjoint_gradient(np.zeros((lat.nv, 3)))  # nothing recorded
+    lat.close()
