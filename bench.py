@@ -290,6 +290,49 @@ def time_ensemble(steps, warmup, n=96, seed=2305):
             "path": "iblb_batch_step (graph of two steps of every instance), FP32"}
 
 
+def time_adjoint(steps, every, ref_steps=2):
+    """Adjoint steps/s on the 64^3 wetting workload (FP64): iblb_adjoint_record of `steps`
+    steps with a state copy every `every`, then iblb_adjoint_gradient of the wetted radius
+    (torch observable); the autograd reference (oracle/adjoint.py, one host thread) is timed on
+    `ref_steps` steps of the same workload."""
+    import torch
+    from paper_2305_18919_gb300 import adjoint as ad
+    from paper_2305_18919_gb300 import binding
+    wl = inputs.adjoint_wetting_64()
+    _, faces = wl.mesh()
+    lat = binding.Lattice.from_workload(wl, precision="fp64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.adjoint_record(steps, every)
+    t_fwd = time.perf_counter() - t0
+    qt = torch.tensor(lat.vertices(), requires_grad=True)
+    radius = ad.wetted_radius(qt, faces)
+    (dJdq,) = torch.autograd.grad(radius, qt)
+    t0 = time.perf_counter()
+    g = lat.adjoint_gradient(dJdq.numpy())
+    t_adj = time.perf_counter() - t0
+    lat.close()
+    out = {"workload": wl.name, "steps": steps, "checkpoint_every": every,
+           "value": round(steps / t_adj, 1), "unit": "adjoint steps/s",
+           "forward_steps_per_s": round(steps / t_fwd, 1),
+           "observable": "wetted radius", "J": round(float(radius), 4),
+           "dJ_dtheta": [float(x) for x in g],
+           "path": "iblb_adjoint_record + iblb_adjoint_gradient (recompute per segment + reverse step), FP64"}
+    try:
+        torch.set_num_threads(1)
+        from oracle import adjoint as oa
+        t0 = time.perf_counter()
+        oa.gradient(wl, ref_steps, lambda q: ad.wetted_radius(q, faces))
+        t_ref = time.perf_counter() - t0
+        out["reference"] = {"value": round(ref_steps / t_ref, 4), "unit": "adjoint steps/s",
+                            "cores": 1, "kind": "oracle",
+                            "sample": f"{ref_steps} steps forward and reverse with autograd "
+                                      "(float64 PyTorch restatement of the oracle, one thread)"}
+    except Exception as e:  # the reference needs torch with autograd on the host
+        out["reference"] = {"unavailable": str(e)[:200]}
+    return out
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     from paper_2305_18919_gb300 import binding
@@ -395,6 +438,8 @@ def run_gpu(args, wl, rank, world):
         line["precision_variants"] = variants
     if rank == 0 and world == 1 and args.ensemble_steps > 0 and wl.name.startswith("shear256"):
         line["ensemble"] = time_ensemble(args.ensemble_steps, 10)
+    if rank == 0 and world == 1 and args.adjoint_steps > 0 and wl.name.startswith("shear256"):
+        line["adjoint"] = time_adjoint(args.adjoint_steps, 100)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -408,6 +453,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="shear256")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--adjoint-steps", type=int, default=5000,
+                    help="steps of the 64^3 adjoint workload timed beside the headline (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=200,
                     help="steps timed for the 96-box batched ensemble reported beside the "
                          "headline (0: skip)")

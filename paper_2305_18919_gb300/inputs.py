@@ -215,6 +215,22 @@ def wetting_ensemble(n: int = 96, seed: int = 2305, edges=(48, 64, 80, 96),
     return out
 
 
+def adjoint_wetting_64(eps_over_alpha: float = 1.0) -> Workload:
+    """The adjoint workload: a 64^3 box with walls at z = 0 and 63, a softly coated particle
+    (Table I) of R = 12, icosphere subdivision 4 (2562 vertices, 5120 faces), at the LJ minimum
+    above the bottom wall (reading R12), alpha_bar = 0.01, eps = eps_over_alpha * alpha_bar,
+    tau = 1, FP64 (the adjoint's precision), 5000 steps with a state copy every 100."""
+    abar, r = 0.01, 12.0
+    zc = 0.5 + r + 2.0 ** (1.0 / 6.0) * LJ_XI
+    return Workload(
+        name=f"adjoint_wetting64_sub4_eps{eps_over_alpha:g}", nx=64, ny=64, nz=64, tau=1.0,
+        wall_u_bottom=(0.0, 0.0, 0.0), wall_u_top=(0.0, 0.0, 0.0),
+        subdivisions=4, radius=r, centre=(32.0, 32.0, zc),
+        alpha=tuple(abar * a for a in ALPHA_CLASSES["softly_coated"]),
+        eps=eps_over_alpha * abar, wall_force_on=1, volume_force_on=1, steps=5000,
+        precision="fp64", extra={"checkpoint_every": 100})
+
+
 def scaled_shear(n: int, subdivisions: int, radius: float, tau: float = 1.0,
                  wall_u: float = 0.01, alpha=(0.01, 0.0, 0.0), precision: str = "fp32",
                  nx: int | None = None, ny: int | None = None) -> Workload:

@@ -92,3 +92,55 @@ def test_adjoint_rejects_what_it_cannot_do():
     with pytest.raises(binding.IBLBError):
         lat.adjoint_gradient(np.zeros((lat.nv, 3)))  # nothing recorded
     lat.close()
+
+
+def _masked_fd(wl, N, obs, grad, select):
+    """Central differences of obs(q_N) over GPU runs, with the observable's vertex or face
+    selection held at the base run's."""
+    from paper_2305_18919_gb300 import binding
+
+    def J(params):
+        w = copy.deepcopy(wl)
+        w.alpha, w.eps = tuple(params[:3]), params[3]
+        lat = binding.Lattice.from_workload(w, precision="fp64")
+        lat.step(N)
+        q = torch.tensor(lat.vertices())
+        lat.close()
+        return float(obs(q, select))
+
+    p0 = np.array(list(wl.alpha) + [wl.eps])
+    for k in range(4):
+        h = 1e-3 * max(abs(p0[k]), 1e-3)  # a parameter may be 0 (alpha2 of this class)
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (J(pp) - J(pm)) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-4 * abs(fd) + 1e-9 * abs(grad).max()
+
+
+def test_autograd_function_contact_angle_and_wetted_radius():
+    """torch.autograd through the adjoint (paper_2305_18919_gb300.adjoint.run) for the apparent
+    contact angle and the wetted radius, against central differences of GPU runs."""
+    from paper_2305_18919_gb300 import adjoint as ad
+    wl = inputs.scaled_wetting(32, 24, 3, 6.0, alpha=(2e-3, 0.0, 2e-3), eps=2e-3,
+                               precision="fp64")
+    _, faces = wl.mesh()
+    N = 120
+    theta = torch.tensor(list(wl.alpha) + [wl.eps], dtype=torch.float64, requires_grad=True)
+    q = ad.run(theta, wl, N, every=40)
+    # the angle with a plane through the lower half of the particle: the droplet has not
+    # spread yet after 120 steps, so the circle does not reach the wall plane itself
+    z_ref = wl.centre[2] - 0.5 * wl.radius
+    sel_v = ad.contact_angle_selection(q, faces, z_wall=z_ref, exclude=0.0)
+    theta_deg = ad.contact_angle(q, faces, z_wall=z_ref, select=sel_v)
+    assert 90 < float(theta_deg.detach()) < 180
+    (g_angle,) = torch.autograd.grad(theta_deg, theta)
+    q = ad.run(theta, wl, N, every=40)
+    gz = (q[faces[:, 0], 2] + q[faces[:, 1], 2] + q[faces[:, 2], 2]).detach() / 3
+    sel_f = torch.as_tensor(gz - 0.5 < 1.0)
+    r = ad.wetted_radius(q, faces, select=sel_f)
+    assert float(r.detach()) > 0
+    (g_r,) = torch.autograd.grad(r, theta)
+    _masked_fd(wl, N, lambda qq, s: ad.contact_angle(qq, faces, z_wall=z_ref, select=s),
+               g_angle.numpy(), sel_v)
+    _masked_fd(wl, N, lambda qq, s: ad.wetted_radius(qq, faces, select=s), g_r.numpy(), sel_f)
