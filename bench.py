@@ -220,12 +220,24 @@ def replica_mlups(world: int, cells: int, steps: int, seconds: float) -> float:
     return world * cells * steps / seconds / 1e6
 
 
-def time_variant(wl, precision, steps, warmup):
+def k1_kernel_name(lat, precision):
+    """Name of the kernel that runs the full-lattice pass of the timed steps."""
+    storage = {"fp64": "double", "fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}
+    if lat.stream_collide_staged():
+        return f"stream_collide_staged_kernel<{storage[precision]},false>"
+    if precision in ("fp16", "bf16"):
+        return f"stream_collide_quad_kernel<{storage[precision]},false,false>"
+    real = "double" if precision == "fp64" else "float"
+    return f"stream_collide_kernel<{real},{storage[precision]},false,false,false>"
+
+
+def time_variant(wl, precision, steps, warmup, sc=("auto", 0, 0, 0)):
     """Device-timed throughput of the same workload with another population storage type
     (inputs resident, CUDA events on the caller's stream, same step as the headline)."""
     import torch
     from paper_2305_18919_gb300 import binding
     lat = binding.Lattice.from_workload(wl, precision=precision)
+    lat.set_stream_collide(*sc)
     lat.step(max(3, warmup))
     lat.set_profiling(True)
     stream = torch.cuda.current_stream()
@@ -240,6 +252,7 @@ def time_variant(wl, precision, steps, warmup):
     k1_ms, k1_launches, _ = lat.profile()
     bpc = lat.bytes_per_cell()
     sms = lat.interface_sms()
+    kernel = k1_kernel_name(lat, precision)
     lat.close()
     fluid = wl.nx * wl.ny * (wl.nz - 2)
     peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
@@ -248,7 +261,7 @@ def time_variant(wl, precision, steps, warmup):
             "ms_per_step": round(ms / steps, 5), "steps": steps, "bytes_per_cell": bpc,
             "k1_ms_avg": round(k1_avg, 5),
             "k1_frac": round(bpc * fluid / (k1_avg * 1e-3) / 1e9 / peak, 4),
-            "interface_sms": sms}
+            "interface_sms": sms, "kernel": kernel}
 
 
 def time_ensemble(steps, warmup, n=96, seed=2305):
@@ -345,7 +358,8 @@ def run_gpu(args, wl, rank, world):
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     lat = binding.Lattice.from_workload(wl, precision=wl.precision, ib_sms=args.ib_sms)
-    storage = {"fp64": "double", "fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}
+    sc = (args.stream_collide, args.stages, args.stage_warps, args.stage_rows)
+    lat.set_stream_collide(*sc)
     lat.step(max(3, args.warmup))
     torch.cuda.synchronize()
 
@@ -398,8 +412,7 @@ def run_gpu(args, wl, rank, world):
     achieved = bpc * fluid / (k1_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": f"stream_collide_kernel<{'double' if wl.precision == 'fp64' else 'float'},"
-                          f"{storage[wl.precision]},false,false>",
+                "kernel": k1_kernel_name(lat, wl.precision),
                 "algorithmic_bytes_per_launch": bpc * fluid,
                 "k1_ms_avg": round(k1_avg_ms, 5), "peak_source": peak_note,
                 "step_frac": round(bpc * fluid / (ms_step * 1e-3) / 1e9 / peak, 4)}
@@ -412,7 +425,7 @@ def run_gpu(args, wl, rank, world):
     lat.close()
     variants = None
     if rank == 0 and world == 1 and args.variant_steps > 0 and wl.precision == "fp32":
-        variants = {p: time_variant(wl, p, args.variant_steps, args.warmup)
+        variants = {p: time_variant(wl, p, args.variant_steps, args.warmup, sc)
                     for p in ("fp16", "bf16")}
         variants["note"] = ("populations stored in 16 bits as (f_i - w_i rho0) K / w_i, FP32 "
                             "collision; errors against the FP64 oracle in tests/test_gpu_precision.py")
@@ -466,6 +479,16 @@ def main():
                          "arithmetic)")
     ap.add_argument("--ib-sms", type=int, default=0,
                     help="SMs for the interface chain (0: library default, <0: no partition)")
+    ap.add_argument("--stream-collide", default="auto", choices=["auto", "staged", "direct"],
+                    help="kernel of the full-lattice pass: rows staged in shared memory by bulk "
+                         "copies, loaded directly by each thread, or the library's choice for "
+                         "the storage type (auto)")
+    ap.add_argument("--stages", type=int, default=0, help="buffers per block of the staged pass "
+                                                           "(0: library default)")
+    ap.add_argument("--stage-warps", type=int, default=0,
+                    help="compute warps per block of the staged pass (0: library default)")
+    ap.add_argument("--stage-rows", type=int, default=0,
+                    help="lattice rows per unit of the staged pass (0: library default)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -238,6 +238,44 @@ int iblb_adjoint_record(iblb_ctx *ctx, int32_t nsteps, int32_t every);
 int iblb_adjoint_gradient(iblb_ctx *ctx, const double *dJdq, double *dJdtheta);
 int iblb_adjoint_release(iblb_ctx *ctx);
 
+/* Kernel of the full-lattice stream-collide pass (pull streaming with Eqs. 9-10) from the
+   second step of a run on (the first step after an initialisation reads the state in place and
+   always takes the direct kernel).
+   IBLB_STREAM_COLLIDE_STAGED: a persistent kernel, one block per SM of the lattice partition.
+     The lattice is cut into units of `rows` consecutive lattice rows (y) of one layer (z); one
+     warp of each block copies what the next units pull, 19 blocks of `rows` population rows,
+     into shared memory with bulk asynchronous copies completing on mbarriers, `stages` buffers
+     deep, and `warps` compute warps collide from there. Applies to IBLB_FP32, IBLB_FP16 and
+     IBLB_BF16 when nx values of the storage type are a whole number of 16-byte blocks and two
+     buffers fit in shared memory; otherwise the direct kernel runs.
+   IBLB_STREAM_COLLIDE_DIRECT: every thread loads its nodes' populations from global memory.
+   IBLB_STREAM_COLLIDE_AUTO (default): staged for 16-bit storage, direct otherwise (the faster
+     of the two on GB300 for each storage type).
+   Both kernels give the same populations bit for bit. stages: 0 (4) or 2..8, reduced to what
+   fits in shared memory; warps: 0 (8) or 1..8; rows: 0 (as many as keep one copy within 4 KB)
+   or a power of two up to 16 that divides ny. IBLB_EINVAL for anything else. A staged block
+   whose wait for its copies gives up (after 1 s) returns early, and iblb_step then returns
+   IBLB_ECUDA. */
+#define IBLB_STREAM_COLLIDE_AUTO 0
+#define IBLB_STREAM_COLLIDE_STAGED 1
+#define IBLB_STREAM_COLLIDE_DIRECT 2
+int iblb_set_stream_collide(iblb_ctx *ctx, int32_t kind, int32_t stages, int32_t warps,
+                            int32_t rows);
+/* Limit in nanoseconds of each wait of the staged kernel's warps for a buffer to fill or to be
+   released, on the GPU's global timer (default 1e9, range 0 .. 6e10; 0: a single non-blocking
+   test, so that a block's first wait, which comes before its copies complete, gives up; this
+   exercises the timeout path). A wait that runs out records the timeout in the health word
+   and its block stops; before the block exits, its copying warp still waits up to 1 s for the
+   copies it has in flight. iblb_step then returns IBLB_ECUDA and the populations of that step
+   are incomplete; the context stays usable (iblb_init_equilibrium or iblb_load_state restore
+   a state). IBLB_EINVAL outside the range. */
+int iblb_set_stage_wait_limit(iblb_ctx *ctx, int64_t ns);
+
+/* 1 if the stream-collide steps after the first take the staged kernel (as configured by
+   iblb_set_stream_collide for this lattice and storage type), 0 for the direct kernel, -1 for
+   a NULL context. */
+int32_t iblb_stream_collide_staged(const iblb_ctx *ctx);
+
 /* SMs of the interface partition of iblb_step (0: no partition, -1: NULL context). */
 int32_t iblb_interface_sms(const iblb_ctx *ctx);
 

@@ -23,6 +23,9 @@ IBLB_FP64 = 1
 IBLB_FP32 = 2
 IBLB_FP16 = 3
 IBLB_BF16 = 4
+IBLB_STREAM_COLLIDE_AUTO = 0
+IBLB_STREAM_COLLIDE_STAGED = 1
+IBLB_STREAM_COLLIDE_DIRECT = 2
 
 _PRECISION = {"fp64": IBLB_FP64, "fp32": IBLB_FP32, "fp16": IBLB_FP16, "bf16": IBLB_BF16}
 
@@ -81,6 +84,9 @@ SIGNATURES = {
     "iblb_profile": (_i32, [_vp, _dp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "iblb_bytes_per_cell": (_i64, [_vp]),
     "iblb_interface_sms": (_i32, [_vp]),
+    "iblb_set_stream_collide": (_i32, [_vp, _i32, _i32, _i32, _i32]),
+    "iblb_stream_collide_staged": (_i32, [_vp]),
+    "iblb_set_stage_wait_limit": (_i32, [_vp, _i64]),
     "iblb_mesh_volume_noalloc": (_i32, [_vp, _vp, _i32, _dp, _vp, _vp]),
     "iblb_batch_create": (_i32, [ctypes.POINTER(iblb_lattice_desc), _i32, _vp, ctypes.POINTER(_vp)]),
     "iblb_batch_destroy": (None, [_vp]),
@@ -322,6 +328,23 @@ class Lattice:
 
     def interface_sms(self) -> int:
         return int(self._L.iblb_interface_sms(self.h))
+
+    def set_stage_wait_limit(self, ns):
+        """Limit (ns) of each wait of the staged stream-collide kernel (iblb_set_stage_wait_limit)."""
+        self._check(self._L.iblb_set_stage_wait_limit(self.h, int(ns)))
+
+    def stream_collide_staged(self) -> bool:
+        """Whether the steps after the first take the staged stream-collide kernel."""
+        return bool(self._L.iblb_stream_collide_staged(self.h))
+
+    def set_stream_collide(self, kind="auto", stages=0, warps=0, rows=0):
+        """Kernel of the stream-collide pass from the second step on: "staged" (population rows
+        copied into shared memory by a producer warp: `stages` buffers, `warps` compute warps,
+        units of `rows` lattice rows; 0 for the defaults), "direct", or "auto" (staged for
+        16-bit storage) (iblb_set_stream_collide)."""
+        k = {"auto": IBLB_STREAM_COLLIDE_AUTO, "staged": IBLB_STREAM_COLLIDE_STAGED,
+             "direct": IBLB_STREAM_COLLIDE_DIRECT}[kind]
+        self._check(self._L.iblb_set_stream_collide(self.h, k, int(stages), int(warps), int(rows)))
 
     # --- adjoint ---------------------------------------------------------------------
     def adjoint_record(self, nsteps, every=100):

@@ -82,6 +82,8 @@ int read_health(Ctx &c, int *h) {
 
 // An unstable run reports that first: its garbage positions can also leave tiles unmarked.
 int health_error(Ctx &c, int h) {
+  if (h & iblb::H_TIMEOUT)
+    return fail(c, IBLB_ECUDA, "stream-collide pipeline: a bounded wait for staged data gave up");
   const int unstable = iblb::H_NAN | iblb::H_FAST | iblb::H_WALL | iblb::H_VOLUME;
   if (!(h & unstable))
     return fail(c, IBLB_ECAPACITY, "active-tile table capacity exceeded");
@@ -174,6 +176,7 @@ bool make_partitions(Ctx &c, int want, int prio_hi) {
   c.ib = (cudaStream_t)si;
   c.ls = (cudaStream_t)sl;
   c.ib_sms = (int)part.sm.smCount;
+  c.lat_sms = (int)rest.sm.smCount;
   return true;
 }
 
@@ -289,6 +292,8 @@ int iblb_create(const iblb_lattice_desc *d, void *cuda_stream, iblb_ctx **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&c.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc_bytes(&c.f[b], (size_t)iblb::Q * c.ncell * c.pop_size);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.f[0], 0, (size_t)iblb::Q * c.ncell * c.pop_size, c.stream);
   // The interface chain runs on its own partition of SMs (default 32) so that the concurrent
@@ -807,6 +812,38 @@ int iblb_profile(iblb_ctx *h, double *k1_ms, int64_t *k1_launches, int64_t *kern
   *k1_launches = c.k1_launches;
   *kernel_launches = c.kernel_launches;
   return IBLB_OK;
+}
+
+int iblb_set_stream_collide(iblb_ctx *h, int32_t kind, int32_t stages, int32_t warps,
+                            int32_t rows) {
+  if (!h) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (kind != IBLB_STREAM_COLLIDE_AUTO && kind != IBLB_STREAM_COLLIDE_STAGED &&
+      kind != IBLB_STREAM_COLLIDE_DIRECT)
+    return fail(c, IBLB_EINVAL, "stream-collide kind must be AUTO (0), STAGED (1) or DIRECT (2)");
+  if (stages != 0 && (stages < 2 || stages > 8))
+    return fail(c, IBLB_EINVAL, "stages must be 0 or 2..8");
+  if (warps < 0 || warps > 8) return fail(c, IBLB_EINVAL, "warps must be 0 or 1..8");
+  if (rows < 0 || rows > 16 || (rows & (rows - 1)) || (rows && c.ny % rows))
+    return fail(c, IBLB_EINVAL, "rows must be 0 or a power of two up to 16 that divides ny");
+  c.k1_kind = kind;
+  c.k1_stages = stages;
+  c.k1_warps = warps;
+  c.k1_unit_rows = rows;
+  c.config_gen++;
+  return IBLB_OK;
+}
+
+int iblb_set_stage_wait_limit(iblb_ctx *h, int64_t ns) {
+  if (!h) return IBLB_EINVAL;
+  if (ns < 0 || ns > 60000000000ll) return fail(h->c, IBLB_EINVAL, "wait limit must be 0 .. 60 s");
+  h->c.stage_wait_ns = (unsigned long long)ns;
+  h->c.config_gen++;
+  return IBLB_OK;
+}
+
+int32_t iblb_stream_collide_staged(const iblb_ctx *h) {
+  return h ? (iblb::stream_collide_staged(h->c) ? 1 : 0) : -1;
 }
 
 int32_t iblb_interface_sms(const iblb_ctx *h) { return h ? h->c.ib_sms : -1; }

@@ -43,6 +43,13 @@ constexpr int BUCKET_CAP = 64;
 
 // Health word bits (read back by iblb_step).
 constexpr int H_NAN = 1, H_FAST = 2, H_WALL = 4, H_VOLUME = 8, H_CAPACITY = 16;
+// a bounded wait of the staged stream-collide pipeline gave up (the kernel returned early)
+constexpr int H_TIMEOUT = 32;
+
+// Default shape of the staged stream-collide pass: stages per block, compute warps per block.
+constexpr int kStages = 4, kStageWarps = 8;
+// Default size of one population's copy in the staged pass (bytes): rows per unit follow.
+constexpr size_t kStageCopyBytes = 4096;
 
 // Force and velocity blocks of the active tiles are [slot][64 nodes] of these: x, y, z and one
 // pad, so that each node is one aligned vector access.
@@ -76,6 +83,7 @@ struct Ctx {
   cudaStream_t ib = nullptr;       // library stream: the interface chain of each step
   void *green[2] = {nullptr, nullptr};  // SM partitions (CUgreenCtx): [0] interface, [1] lattice
   int ib_sms = 0;                  // SMs of the interface partition (0: no partition)
+  int lat_sms = 0;                 // SMs of the lattice partition (with a partition)
   cudaEvent_t ev_force = nullptr;  // spread force of the step is ready (recorded on ib)
   cudaEvent_t ev_coll = nullptr;   // post-collision populations of the step are complete
   cudaEvent_t ev_sync = nullptr;   // general cross-stream join
@@ -130,6 +138,12 @@ struct Ctx {
   size_t dscratch_len = 0;
   int sm_count = 0;
   int k1_rows = 0;          // lattice rows per block of the stream-collide pass (0: 1)
+  int k1_kind = 0;          // IBLB_STREAM_COLLIDE_STAGED or IBLB_STREAM_COLLIDE_DIRECT
+  int k1_stages = 0;        // stages of the staged pass (0: kStages)
+  int k1_warps = 0;         // compute warps per block of the staged pass (0: kStageWarps)
+  int k1_unit_rows = 0;     // lattice rows per unit of the staged pass (0: by copy size)
+  unsigned long long stage_wait_ns = 1000000000ull;  // limit of a staged pass's waits (ns)
+  int smem_optin = 0;       // shared memory a block may opt in to (bytes)
   uint64_t config_gen = 0;  // bumped by every call that changes what a queued step launches
   std::string err;
 };
@@ -147,6 +161,8 @@ int restore_state(Ctx &c, const void *P, const double *q, int fresh);
 void adjoint_free(Ctx &c);
 // Lattice rows per block of the stream-collide pass (k1_rows within the launch bound).
 int k1_block_rows(const Ctx &c);
+// Whether the stream-collide steps after the first take the staged kernel.
+bool stream_collide_staged(const Ctx &c);
 
 // Launchers (each returns cudaGetLastError() of its launch) on stream `s`.
 // Stream-collide of every fluid node with the body force only (no interface force).

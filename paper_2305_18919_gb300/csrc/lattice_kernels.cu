@@ -536,6 +536,358 @@ __global__ void __launch_bounds__(128) stream_collide_quad_kernel(const S *__res
     *reinterpret_cast<uint2 *>(fout + (size_t)i * P.ncell + n) = make_uint2(lo[i], hi[i]);
 }
 
+// --- K1s: stream-collide with the pulled rows staged in shared memory by bulk copies ----------
+//
+// A unit of work is R lattice rows (y0 .. y0 + R - 1 at one z). The pulled populations of a
+// unit are whole x-rows of the population array: population i of row (y, z) streams from row
+// (y - c_iy, z - c_iz), or, for a link from a wall node, is population opp(i) of row (y, z)
+// itself. A producer warp copies those 19 R rows into a shared-memory stage with cp.async.bulk,
+// their completion counted in bytes on the stage's `full` mbarrier; NC compute warps read the
+// nodes from the stage (the periodic x wrap is an index into the row), collide them and store
+// the results straight to global memory, then release the stage on its `empty` mbarrier. D
+// stages rotate, so the bytes in flight per SM are set by shared memory, not by registers.
+// Every wait is bounded: a wait that gives up records H_TIMEOUT in the health word and the
+// block returns once the producer has waited (again bounded) for its own copies in flight.
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Non-blocking test for the completion of the phase of parity `parity`.
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr unsigned long long kDrainWaitNs = 1000000000ull;  // the wait for copies in flight
+constexpr int kStageWaitPolls = 1 << 26;                     // polls before any wait gives up
+// Wait for the completion of the phase of parity `parity`; false if the wait gave up (after
+// limit_ns nanoseconds of the global timer) or another warp of the block raised `abort_flag`
+// meanwhile. limit_ns = 0: one non-blocking test.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          const volatile int *abort_flag,
+                                          unsigned long long limit_ns) {
+  if (limit_ns == 0) return mbar_test_wait(bar, parity);
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int k = 0; k < kStageWaitPolls; k++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag || global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to
+// shared memory, completing `bytes` transactions on mbarrier `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Shape of the staged pass: units of R rows, D stages of R * 19 rows of nx values each.
+struct StageGeom {
+  int z0;            // first fluid layer
+  int units_per_z;   // ny / R
+  int nunits;        // units_per_z * fluid layers
+  int R, D;
+  int stage_elems;   // R * 19 * nx
+  unsigned long long wait_ns;  // limit of a wait for a stage or for a free stage
+};
+
+// Bytes ahead of the first stage: the 2 D mbarriers and the abort flag.
+constexpr int kStageHeader = 256;
+
+// Row (z, wall flags) of a unit. Links from a wall exist only on the first and last fluid
+// layer, and they are the same for every row of the unit.
+struct UnitRows {
+  int z, y0, zm, zp;
+  bool wall_below, wall_above;
+};
+template <typename real>
+__device__ __forceinline__ UnitRows unit_rows(int unit, const LatParams<real> &P,
+                                              const StageGeom &G) {
+  UnitRows u;
+  u.z = G.z0 + unit / G.units_per_z;
+  u.y0 = (unit % G.units_per_z) * G.R;
+  u.zm = u.z - 1;
+  u.zp = u.z + 1;
+  if (!P.has_walls) {
+    u.zm = u.z == 0 ? P.nz - 1 : u.zm;
+    u.zp = u.z == P.nz - 1 ? 0 : u.zp;
+  }
+  u.wall_below = P.has_walls && u.zm == 0;
+  u.wall_above = P.has_walls && u.zp == P.nz - 1;
+  return u;
+}
+
+// Signs of c_iy and c_iz as bit masks over i, for run-time direction indices.
+__host__ __device__ constexpr unsigned dir_mask(int axis, int sign) {
+  unsigned m = 0;
+  for (int i = 0; i < Q; i++) {
+    const int c = axis == 1 ? cy(i) : cz(i);
+    if (c == sign) m |= 1u << i;
+  }
+  return m;
+}
+constexpr unsigned kYPos = dir_mask(1, 1), kYNeg = dir_mask(1, -1);
+constexpr unsigned kZPos = dir_mask(2, 1), kZNeg = dir_mask(2, -1);
+__device__ __forceinline__ int dir_c(unsigned pos, unsigned neg, int i) {
+  return (int)((pos >> i) & 1u) - (int)((neg >> i) & 1u);
+}
+
+// Producer lanes: queue the copies of `unit` into `stage` (lane 0 has armed `full` with the
+// byte count). The stage holds [19][R][nx] values: block i is population i of lattice rows
+// y0 .. y0 + R - 1 as pulled, or population opp(i) of those rows for a link from the wall. The
+// R source rows of a population are consecutive rows of one plane, so one copy brings them,
+// or two where they wrap around y.
+template <typename S>
+__device__ __forceinline__ void stage_issue(const S *__restrict__ fin, S *stage,
+                                            unsigned long long *full, const UnitRows &u,
+                                            const LatParams<float> &P, const StageGeom &G,
+                                            int lane) {
+  if (lane >= Q) return;
+  const int i = lane;
+  const unsigned row_bytes = (unsigned)(P.nx * sizeof(S));
+  const size_t plane = (size_t)P.nx * P.ny;
+  const int ciy = dir_c(kYPos, kYNeg, i);
+  const int ciz = dir_c(kZPos, kZNeg, i);
+  S *dst = stage + (size_t)i * G.R * P.nx;
+  if ((ciz > 0 && u.wall_below) || (ciz < 0 && u.wall_above)) {
+    const size_t src = (size_t)opp(i) * P.ncell + (size_t)u.z * plane + (size_t)u.y0 * P.nx;
+    bulk_g2s(dst, fin + src, G.R * row_bytes, full);
+    return;
+  }
+  const int zs = ciz > 0 ? u.zm : (ciz < 0 ? u.zp : u.z);
+  const S *pop = fin + (size_t)i * P.ncell + (size_t)zs * plane;
+  const int ys = u.y0 - ciy;  // source of row y0; rows ys .. ys + R - 1 follow (mod ny)
+  if (ys < 0) {               // row y0 = 0 pulls from row ny - 1
+    bulk_g2s(dst, pop + (size_t)(P.ny - 1) * P.nx, row_bytes, full);
+    if (G.R > 1) bulk_g2s(dst + P.nx, pop, (G.R - 1) * row_bytes, full);
+  } else if (ys + G.R > P.ny) {  // the last row of the unit pulls from row 0
+    if (G.R > 1) bulk_g2s(dst, pop + (size_t)ys * P.nx, (G.R - 1) * row_bytes, full);
+    bulk_g2s(dst + (size_t)(G.R - 1) * P.nx, pop, row_bytes, full);
+  } else {
+    bulk_g2s(dst, pop + (size_t)ys * P.nx, G.R * row_bytes, full);
+  }
+}
+
+// Compute lanes, FP32 storage: the node pair (x0, x0 + 1) of one lattice row, whose pulled
+// population i is the stage row rows + i * stride, collided and stored at node n of fout.
+template <bool FORCE>
+__device__ __forceinline__ void staged_pair(const float *rows, int stride, int x0,
+                                            const UnitRows &u, const LatParams<float> &P,
+                                            float *__restrict__ fout, size_t n) {
+  const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;  // source of node x0 for c_x = +1
+  const int xp = x0 + 2 == P.nx ? 0 : x0 + 2;  // source of node x0 + 1 for c_x = -1
+  float a[Q], b[Q];
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const float *row = rows + i * stride;
+    if ((cz(i) > 0 && u.wall_below) || (cz(i) < 0 && u.wall_above)) {
+      const float2 v = *reinterpret_cast<const float2 *>(row + x0);
+      const float wall = cz(i) > 0 ? P.wb[i] : P.wt[i];
+      a[i] = v.x + wall;
+      b[i] = v.y + wall;
+    } else if (cx(i) == 0) {
+      const float2 v = *reinterpret_cast<const float2 *>(row + x0);
+      a[i] = v.x;
+      b[i] = v.y;
+    } else if (cx(i) > 0) {
+      a[i] = row[xm];
+      b[i] = row[x0];
+    } else {
+      a[i] = row[x0 + 1];
+      b[i] = row[xp];
+    }
+  }
+  const float F[3] = {P.g[0], P.g[1], P.g[2]};
+  collide<float, FORCE>(a, F, P);
+  collide<float, FORCE>(b, F, P);
+  store_pair(fout, P, n, a, b);
+}
+
+// Compute lanes, 16-bit storage: the four nodes x0 .. x0 + 3 (as in K1's 16-bit form, with
+// the rows read from the stage).
+template <typename S, bool FORCE>
+__device__ __forceinline__ void staged_quad(const S *rows, int stride, int x0, const UnitRows &u,
+                                            const LatParams<float> &P, S *__restrict__ fout,
+                                            size_t n) {
+  using V2 = typename Storage<S>::V2;
+  const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;  // source of node x0 for c_x = +1
+  const int xp = x0 + 4 == P.nx ? 0 : x0 + 4;  // source of node x0 + 3 for c_x = -1
+  unsigned int lo[Q], hi[Q];
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const S *row = rows + i * stride;
+    const uint2 v = *reinterpret_cast<const uint2 *>(row + x0);
+    const bool bounced = (cz(i) > 0 && u.wall_below) || (cz(i) < 0 && u.wall_above);
+    if (bounced || cx(i) == 0) {
+      lo[i] = v.x;
+      hi[i] = v.y;
+    } else if (cx(i) > 0) {  // sources x0 - 1 .. x0 + 2
+      const unsigned int e = *reinterpret_cast<const unsigned short *>(row + xm);
+      lo[i] = __byte_perm(e, v.x, 0x5410);
+      hi[i] = __byte_perm(v.x, v.y, 0x5432);
+    } else {  // sources x0 + 1 .. x0 + 4
+      const unsigned int e = *reinterpret_cast<const unsigned short *>(row + xp);
+      lo[i] = __byte_perm(v.x, v.y, 0x5432);
+      hi[i] = __byte_perm(v.y, e, 0x5432);
+    }
+  }
+  const float F[3] = {P.g[0], P.g[1], P.g[2]};
+#pragma unroll
+  for (int h = 0; h < 2; h++) {  // node pairs (x0, x0 + 1), (x0 + 2, x0 + 3)
+    unsigned int *pk = h ? hi : lo;
+    float2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      g[i] = widen_pair(as_pair<V2>(pk[i]));
+      if ((cz(i) > 0 && u.wall_below) || (cz(i) < 0 && u.wall_above)) {
+        const float wall = (cz(i) > 0 ? P.wb[i] : P.wt[i]) * float(kscale<S>(i));
+        g[i] = add2(g[i], dup(wall));
+      }
+    }
+    collide_pair_scaled<FORCE>(g, F, P, float(Storage<S>::K));
+#pragma unroll
+    for (int i = 0; i < Q; i++) pk[i] = as_bits(narrow_pair<V2>(g[i]));
+  }
+#pragma unroll
+  for (int i = 0; i < Q; i++)
+    *reinterpret_cast<uint2 *>(fout + (size_t)i * P.ncell + n) = make_uint2(lo[i], hi[i]);
+}
+
+// K1s: persistent staged stream-collide (not the first step of a run). blockDim.x = 32 (NC + 1), NC <= 8:
+// warps 0 .. NC-1 compute, warp NC produces. Block b takes units b, b + gridDim.x, ...
+// NPT nodes per compute lane: 2 for FP32, 4 for 16-bit storage.
+template <typename S, bool FORCE>
+__global__ void __launch_bounds__(288, 1) stream_collide_staged_kernel(
+    const S *__restrict__ fin, S *__restrict__ fout, const LatParams<float> P,
+    const StageGeom G, int *__restrict__ health) {
+  constexpr int NPT = sizeof(S) == 2 ? 4 : 2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long *full = reinterpret_cast<unsigned long long *>(smem);
+  unsigned long long *empty = full + G.D;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + G.D);
+  S *stages = reinterpret_cast<S *>(smem + kStageHeader);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NC = (blockDim.x >> 5) - 1;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G.D; s++) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, NC);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const int my_units = G.nunits > (int)blockIdx.x
+                           ? (G.nunits - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                           : 0;
+  if (warp == NC) {  // producer
+    int issued = 0;
+    for (int k = 0; k < my_units; k++) {
+      const int s = k % G.D;
+      if (k >= G.D) {  // stage s is free once every compute warp released unit k - D
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait(empty + s, ((k / G.D) - 1) & 1, abort_flag, G.wait_ns);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) {
+            *abort_flag = 1;
+            atomicOr(health, H_TIMEOUT);
+          }
+          break;
+        }
+      }
+      const UnitRows u = unit_rows(blockIdx.x + k * gridDim.x, P, G);
+      S *stage = stages + (size_t)s * G.stage_elems;
+      if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(full + s, (unsigned)(G.R * Q * P.nx * sizeof(S)));
+      }
+      __syncwarp();
+      stage_issue(fin, stage, full + s, u, P, G, lane);
+      issued = k + 1;
+    }
+    // copies still in flight land before the block exits: those of the last D units issued
+    // (a unit before them was waited for by every compute warp before its stage was reused)
+    if (lane == 0) {
+      const int no_abort = 0;
+      for (int k = issued - G.D < 0 ? 0 : issued - G.D; k < issued; k++)
+        if (!mbar_wait(full + k % G.D, (k / G.D) & 1, &no_abort, kDrainWaitNs))
+          atomicOr(health, H_TIMEOUT);
+    }
+    return;
+  }
+  // compute warps
+  const int per_row = P.nx / NPT;
+  const size_t plane = (size_t)P.nx * P.ny;
+  for (int k = 0; k < my_units; k++) {
+    const int s = k % G.D;
+    if (!__all_sync(0xffffffffu, mbar_wait(full + s, (k / G.D) & 1, abort_flag, G.wait_ns))) {
+      if (lane == 0) {
+        *abort_flag = 1;
+        atomicOr(health, H_TIMEOUT);
+      }
+      return;
+    }
+    const UnitRows u = unit_rows(blockIdx.x + k * gridDim.x, P, G);
+    const S *stage = stages + (size_t)s * G.stage_elems;
+    for (int w = warp * 32 + lane; w < G.R * per_row; w += NC * 32) {
+      const int r = w / per_row, x0 = NPT * (w - r * per_row);
+      const size_t n = (size_t)u.z * plane + (size_t)(u.y0 + r) * P.nx + x0;
+      if constexpr (sizeof(S) == 2)
+        staged_quad<S, FORCE>(stage + (size_t)r * P.nx, G.R * P.nx, x0, u, P, fout, n);
+      else
+        staged_pair<FORCE>(stage + (size_t)r * P.nx, G.R * P.nx, x0, u, P, fout, n);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + s);
+  }
+}
+
 // K1t: stream-collide of the fluid nodes of the active tiles with body + interface force,
 // one warp per tile (grid-stride), each thread the node pair (x0, x0 + 1) of a tile row as in
 // K1. Runs after K1 of the same step and overwrites those nodes. Pairs whose interface force
@@ -721,8 +1073,94 @@ cudaError_t stream_collide_quad_t(Ctx &c, int first, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Shape of the staged pass on context c (false where it does not apply: a row of the storage
+// type that is not a whole number of 16-byte blocks, or too little shared memory for two
+// stages). R lattice rows per unit (`rows`, or by default as many as keep one population's
+// copy within kStageCopyBytes): the copies are few and large, which the copy engine needs.
+template <typename S>
+bool stage_geom(const Ctx &c, int stages, int rows, StageGeom &G, size_t &smem) {
+  constexpr int NPT = sizeof(S) == 2 ? 4 : 2;
+  const size_t row_bytes = (size_t)c.nx * sizeof(S);
+  if (row_bytes % 16 != 0 || c.nx % NPT != 0) return false;
+  auto fits = [&](int r, int d) { return kStageHeader + (size_t)d * r * Q * row_bytes <= (size_t)c.smem_optin; };
+  int R = rows;
+  if (R <= 0) {
+    R = 1;
+    while (R < 16 && c.ny % (2 * R) == 0 && 2 * R * row_bytes <= kStageCopyBytes && fits(2 * R, 2))
+      R *= 2;
+  }
+  if (c.ny % R != 0 || !fits(R, 2)) return false;
+  const size_t stage_bytes = (size_t)R * Q * row_bytes;
+  int D = stages;
+  while (D > 2 && !fits(R, D)) D--;
+  G.z0 = c.has_walls ? 1 : 0;
+  G.units_per_z = c.ny / R;
+  G.nunits = G.units_per_z * (c.has_walls ? c.nz - 2 : c.nz);
+  G.R = R;
+  G.D = D;
+  G.stage_elems = R * Q * c.nx;
+  G.wait_ns = c.stage_wait_ns;
+  smem = kStageHeader + D * stage_bytes;
+  return true;
+}
+
+template <typename S, bool FORCE>
+cudaError_t launch_staged(Ctx &c, const StageGeom &G, size_t smem, int nc, cudaStream_t st) {
+  auto kern = stream_collide_staged_kernel<S, FORCE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // one block per SM of the lattice partition, each working through its share of the units
+  const int sms = c.green[0] ? c.lat_sms : c.sm_count;
+  const int grid = G.nunits < sms ? G.nunits : sms;
+  kern<<<grid, 32 * (nc + 1), smem, st>>>((const S *)c.f[c.cur], (S *)c.f[c.cur ^ 1],
+                                          lat_params<float>(c), G, c.counters + 3);
+  return cudaGetLastError();
+}
+
+// The kind of stream-collide kernel asked for, resolved for storage type S: AUTO takes the
+// staged kernel for 16-bit storage, where it is the faster one (for FP32 the direct kernel
+// already runs at the copy bandwidth).
+template <typename S>
+bool staged_kind(const Ctx &c) {
+  if (sizeof(S) == 8 || c.k1_kind == IBLB_STREAM_COLLIDE_DIRECT) return false;
+  return c.k1_kind == IBLB_STREAM_COLLIDE_STAGED || sizeof(S) == 2;
+}
+
+template <typename real, typename S>
+bool uses_staged_t(const Ctx &c) {
+  StageGeom G;
+  size_t smem = 0;
+  return staged_kind<S>(c) &&
+         stage_geom<S>(c, c.k1_stages > 0 ? c.k1_stages : kStages, c.k1_unit_rows, G, smem);
+}
+
+// K1 through the staged kernel where it applies; *used tells whether it did.
+template <typename real, typename S>
+cudaError_t stream_collide_staged_t(Ctx &c, cudaStream_t st, bool *used) {
+  *used = false;
+  if constexpr (sizeof(S) == 8) {
+    return cudaSuccess;
+  } else {
+    const int nc = c.k1_warps > 0 ? c.k1_warps : kStageWarps;
+    const int stages = c.k1_stages > 0 ? c.k1_stages : kStages;
+    StageGeom G;
+    size_t smem = 0;
+    if (!staged_kind<S>(c) || !stage_geom<S>(c, stages, c.k1_unit_rows, G, smem))
+      return cudaSuccess;
+    *used = true;
+    const bool force = c.g[0] != 0.0 || c.g[1] != 0.0 || c.g[2] != 0.0;
+    return force ? launch_staged<S, true>(c, G, smem, nc, st)
+                 : launch_staged<S, false>(c, G, smem, nc, st);
+  }
+}
+
 template <typename real, typename S>
 cudaError_t stream_collide_t(Ctx &c, int first, cudaStream_t st) {
+  if (!first) {
+    bool used = false;
+    const cudaError_t e = stream_collide_staged_t<real, S>(c, st, &used);
+    if (used) return e;
+  }
   if constexpr (sizeof(S) == 2) return stream_collide_quad_t<S>(c, first, st);
   const LatParams<real> P = lat_params<real>(c);
   const int z0 = c.has_walls ? 1 : 0;
@@ -836,6 +1274,8 @@ int k1_block_rows(const Ctx &c) {
     case IBLB_BF16: return FN<float, __nv_bfloat16>(__VA_ARGS__);         \
     default: return FN<float, float>(__VA_ARGS__);                        \
   }
+
+bool stream_collide_staged(const Ctx &c) { IBLB_DISPATCH(c, uses_staged_t, c) }
 
 cudaError_t launch_stream_collide(Ctx &c, int first, cudaStream_t s) {
   IBLB_DISPATCH(c, stream_collide_t, c, first, s)
