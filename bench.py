@@ -188,20 +188,25 @@ def k1_source_hash():
     return h.hexdigest()
 
 
-def k1_traffic_per_node():
-    """DRAM bytes (read + write) per fluid node of one stream-collide launch, from the committed
-    ncu summary, if it was taken on the current kernel source; else None."""
+K1_PROFILES = ("stream_collide_kernel_shear256.md", "stream_collide_staged_kernel_shear256_fp16.md")
+
+
+def k1_traffic_per_node(kernel):
+    """DRAM bytes (read + write) per fluid node of one launch of `kernel` on the 256^3 lattice,
+    from the committed ncu summary that covers it, if that was taken on the current kernel
+    source; else None."""
     import re
-    path = os.path.join(ROOT, "profiles", "stream_collide_kernel_shear256.md")
-    try:
-        text = open(path).read()
-    except OSError:
-        return None
-    m = re.search(r"traffic per fluid node: ([0-9.]+) B", text)
-    hsh = re.search(r"kernel source sha256: ([0-9a-f]{64})", text)
-    if not m or not hsh or hsh.group(1) != k1_source_hash():
-        return None
-    return float(m.group(1))
+    for name in K1_PROFILES:
+        try:
+            text = open(os.path.join(ROOT, "profiles", name)).read()
+        except OSError:
+            continue
+        k = re.search(r"- kernel: `([^`]+)`", text)
+        m = re.search(r"traffic per fluid node: ([0-9.]+) B", text)
+        hsh = re.search(r"kernel source sha256: ([0-9a-f]{64})", text)
+        if k and k.group(1) == kernel and m and hsh and hsh.group(1) == k1_source_hash():
+            return float(m.group(1))
+    return None
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
@@ -253,6 +258,7 @@ def time_variant(wl, precision, steps, warmup, sc=("auto", 0, 0, 0)):
     bpc = lat.bytes_per_cell()
     sms = lat.interface_sms()
     kernel = k1_kernel_name(lat, precision)
+    per_node = k1_traffic_per_node(kernel) if wl.nx == 256 else None
     lat.close()
     fluid = wl.nx * wl.ny * (wl.nz - 2)
     peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
@@ -261,7 +267,8 @@ def time_variant(wl, precision, steps, warmup, sc=("auto", 0, 0, 0)):
             "ms_per_step": round(ms / steps, 5), "steps": steps, "bytes_per_cell": bpc,
             "k1_ms_avg": round(k1_avg, 5),
             "k1_frac": round(bpc * fluid / (k1_avg * 1e-3) / 1e9 / peak, 4),
-            "interface_sms": sms, "kernel": kernel}
+            "interface_sms": sms, "kernel": kernel,
+            "traffic": int(round(per_node * fluid)) if per_node is not None else None}
 
 
 def time_ensemble(steps, warmup, n=96, seed=2305):
@@ -416,9 +423,9 @@ def run_gpu(args, wl, rank, world):
                 "algorithmic_bytes_per_launch": bpc * fluid,
                 "k1_ms_avg": round(k1_avg_ms, 5), "peak_source": peak_note,
                 "step_frac": round(bpc * fluid / (ms_step * 1e-3) / 1e9 / peak, 4)}
-    per_node = k1_traffic_per_node() if wl.precision == "fp32" else None
+    per_node = k1_traffic_per_node(roofline["kernel"]) if wl.nx == 256 else None
     if per_node is not None:
-        # measured at full size on the 256^3 workload, per fluid node (scaled for others)
+        # measured at full size on the 256^3 lattice (one ncu launch), per fluid node
         roofline["traffic"] = int(round(per_node * fluid))
     clocks = clk.summary()
     ib_sms = lat.interface_sms()
