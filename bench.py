@@ -271,16 +271,16 @@ def time_variant(wl, precision, steps, warmup, sc=("auto", 0, 0, 0)):
             "traffic": int(round(per_node * fluid)) if per_node is not None else None}
 
 
-def time_ensemble(steps, warmup, n=96, seed=2305):
+def time_ensemble(steps, warmup, n=96, seed=2305, ib_sms=0):
     """The batched-ensemble workload: n independent wetting boxes of uneven sizes (edges from
-    {48, 64, 80, 96}), advanced together by iblb_batch_step (one CUDA graph launch per two
-    steps) after iblb_batch_tune, against the same boxes stepped one after another."""
+    {48, 64, 80, 96}), advanced together by iblb_batch_step (each kernel of a step one launch
+    over all boxes) after iblb_batch_tune, against the same boxes stepped one after another."""
     import torch
     from paper_2305_18919_gb300 import binding
     wls = inputs.wetting_ensemble(n, seed)
     cells = sum(w.cells for w in wls)
     fluid = sum(w.nx * w.ny * (w.nz - 2) for w in wls)
-    b = binding.Batch.from_workloads(wls)
+    b = binding.Batch.from_workloads(wls, ib_sms=ib_sms)
     rows = b.tune(trials=3)
     b.step(max(4, warmup))
     stream = torch.cuda.current_stream()
@@ -307,7 +307,8 @@ def time_ensemble(steps, warmup, n=96, seed=2305):
             "step_frac": round(152 * fluid / (ms / steps * 1e-3) / 1e9 / peak, 4),
             "sequential_value": round(replica_mlups(1, cells, steps, seq_s), 1),
             "k1_rows_chosen": {str(r): rows.count(r) for r in sorted(set(rows))},
-            "path": "iblb_batch_step (graph of two steps of every instance), FP32"}
+            "path": "iblb_batch_step: each kernel of a step one launch over all instances "
+                    "(8 launches per step), FP32"}
 
 
 def time_adjoint(steps, every, ref_steps=2):

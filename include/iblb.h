@@ -184,27 +184,33 @@ int iblb_mesh_volume_noalloc(const double *q_dev, const int32_t *faces_dev, int3
    runs one box at a time; this is the ensemble form of its parameter sweeps (Sec. V), a library
    service with no counterpart in the paper.
 
-   iblb_batch_create makes n contexts, instance i from descs[i] (ib_sms is ignored: the
-   instances share all SMs), each with its own CUDA stream, and returns the batch in *out. The
-   contexts are configured and read through the single-context calls on the handles that
-   iblb_batch_context returns (borrowed: they stay owned by the batch and are released by
-   iblb_batch_destroy, which synchronises). `cuda_stream` (a cudaStream_t, NULL: legacy default
-   stream) orders the batch against the caller's work.
+   iblb_batch_create makes n contexts, instance i from descs[i], each with its own CUDA stream,
+   and returns the batch in *out. With descs[0].ib_sms > 0 the batch splits the GPU's SMs as a
+   single context does, that many SMs for the interface kernels of every instance and the rest
+   for the stream-collide passes; 0 or < 0 (the default, the faster on ensembles of many
+   meshes) or a device that cannot partition gives no partition. The other descriptors' ib_sms
+   are ignored. The contexts are configured and read through the
+   single-context calls on the handles that iblb_batch_context returns (borrowed: they stay
+   owned by the batch and are released by iblb_batch_destroy, which synchronises).
+   `cuda_stream` (a cudaStream_t, NULL: legacy default stream) orders the batch against the
+   caller's work.
 
    iblb_batch_step advances every instance by nsteps coupled steps (the iblb_step sequence).
-   It records two steps of every instance in one CUDA graph, at its first use and again after
-   any instance was reconfigured (mesh, interface parameters, initial state, tuning) or stepped
-   alone by an odd count, and replays that graph: one graph launch per two steps for the whole
-   ensemble. A freshly initialised instance takes its first step outside the graph. The call
-   synchronises once at its end and reads every instance's health word: it returns the first
-   failing instance's IBLB_EUNSTABLE / IBLB_ECAPACITY (message in iblb_batch_last_error) and
-   iblb_batch_status fills status[n] with each instance's result. Results are identical, bit
-   for bit, to stepping each context alone without an SM partition.
+   Each kernel of a step is one launch over all instances of a precision (up to 256 per
+   launch), whose blocks read their instance's arguments from tables the batch builds at its
+   first use and again after any instance was reconfigured (mesh, interface parameters,
+   initial state, kernel choice) or stepped alone by an odd count; steps run in pairs, and a
+   freshly initialised instance takes its first step, and an odd last step is taken, through
+   the single-context kernels. The call synchronises once at its end and reads every
+   instance's health word: it returns the first failing instance's IBLB_EUNSTABLE /
+   IBLB_ECAPACITY (message in iblb_batch_last_error) and iblb_batch_status fills status[n]
+   with each instance's result. Results are identical, bit for bit, to stepping each context
+   alone.
 
    iblb_batch_tune picks, per distinct lattice shape and precision, the lattice rows per block
-   (1, 2 or 4, within 128 threads) of the stream-collide pass by timing `trials` launches of
-   each on the instance's own stream (the state is not advanced); iblb_batch_k1_rows reports
-   the choice. */
+   (1, 2 or 4, within 128 threads) of the single-context stream-collide pass (the first and odd
+   steps) by timing `trials` launches of each on the instance's own stream (the state is not
+   advanced); iblb_batch_k1_rows reports the choice. */
 typedef struct iblb_batch iblb_batch;
 int iblb_batch_create(const iblb_lattice_desc *descs, int32_t n, void *cuda_stream,
                       iblb_batch **out);

@@ -385,8 +385,10 @@ class Batch:
                                          _handle=h))
 
     @classmethod
-    def from_workloads(cls, workloads, precision=None, stream=None):
-        b = cls([workload_desc(wl, precision) for wl in workloads], stream)
+    def from_workloads(cls, workloads, precision=None, stream=None, ib_sms=0):
+        """A batch of the workloads' contexts with their meshes; ib_sms: SMs of the batch's
+        interface partition (0: the library default, < 0: no partition)."""
+        b = cls([workload_desc(wl, precision, ib_sms) for wl in workloads], stream)
         for lat, wl in zip(b.contexts, workloads):
             v, f = wl.mesh()
             lat.add_mesh(v, f)

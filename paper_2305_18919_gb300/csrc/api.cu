@@ -241,6 +241,12 @@ bool reference_shape(const double *verts, int nv, const int32_t *faces, int nf, 
 // Upload the reference shape (positions X, per-face data) of the context's mesh.
 int upload_reference(Ctx &c, const double *X, const std::vector<double> &fref,
                      const std::vector<double> &fgeo) {
+  // expected active tiles, for sizing the batched step's grids: the stencils cover a band about
+  // two tiles thick around the surface, A / 8 tiles; twice that allows for the shape changing
+  double area = 0.0;
+  for (size_t j = 3; j < fref.size(); j += 4) area += fref[j];
+  long est = (long)(area / 4.0) + 64;
+  c.tile_estimate = (int)(est < c.max_slots ? est : c.max_slots);
   CUDA_TRY(c, cudaMemcpyAsync(c.fref, fref.data(), fref.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   CUDA_TRY(c, cudaMemcpyAsync(c.xref, X, (size_t)3 * c.nv * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   if (c.precision == IBLB_FP64) {
@@ -512,6 +518,9 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
 }  // extern "C"
 
 namespace iblb {
+
+bool split_sms(Ctx &c, int want, int prio_hi) { return make_partitions(c, want, prio_hi); }
+void release_sms(Ctx &c) { free_partitions(c); }
 
 int enqueue_steps(Ctx &c, int nsteps) {
   // the library streams start after everything queued so far on the context's stream

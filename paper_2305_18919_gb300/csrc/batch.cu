@@ -1,11 +1,16 @@
 // Batched ensemble: many independent IB-LB contexts (lattices and meshes of any sizes)
-// advanced together. Each context runs the same step as iblb_step, on its own stream and
-// without an SM partition; the batch captures two steps of every context into one CUDA graph
-// and replays it, so the instances' small kernels run side by side from one graph launch per
-// two steps instead of one host launch each. Two steps return every context's
-// double-buffer indices (populations, tile maps) to where they started, which is what lets
-// the same graph be replayed. The paper advances one box at a time; this is the ensemble form
-// of its parameter sweeps (Sec. V).
+// advanced together. Each kernel of the coupled step (face forces, vertex gather, the two
+// spreading passes, stream-collide, the active-tile recollision, the shell velocity,
+// interpolation) is one launch over all contexts of a precision: its blocks find their context
+// in a block table and read that context's argument record (the arguments of the context's own
+// launch), then run the same device code as the single-context kernels, so every context ends
+// bit for bit as when stepped alone. The records are built for both parities of a pair of steps
+// (a pair returns the double-buffer indices of populations and tile maps to where they were)
+// and rebuilt when a context changes. The interface chain and the stream-collide passes are
+// queued on two streams joined by events as in a single context's step. The paper advances one
+// box at a time; this is the ensemble form of its parameter sweeps (Sec. V).
+#include <string.h>
+
 #include <algorithm>
 #include <map>
 #include <string>
@@ -16,15 +21,46 @@
 
 using iblb::Ctx;
 
+namespace {
+
+// Instances of one precision, stepped by the same batched launches (at most kMultiMax).
+struct Group {
+  int precision = 0;
+  std::vector<int> members;
+};
+
+// Host image of one batched launch: the records of its instances and its block table.
+struct Table {
+  std::vector<unsigned char> bytes;
+  std::vector<int> start{0};
+  size_t args_off = 0, start_off = 0;
+};
+
+using iblb::MultiKernel;
+constexpr MultiKernel kKernels[] = {iblb::MK_FACE,   iblb::MK_VERTEX,          iblb::MK_SOURCE,
+                                    iblb::MK_GATHER, iblb::MK_STREAM_COLLIDE, iblb::MK_TILES,
+                                    iblb::MK_SHELL,  iblb::MK_INTERP};
+constexpr int kNumKernels = sizeof(kKernels) / sizeof(kKernels[0]);
+constexpr int kPairSteps = 2;  // records are built for both parities of a pair of steps
+
+bool lattice_kernel(MultiKernel k) {
+  return k == iblb::MK_STREAM_COLLIDE || k == iblb::MK_TILES || k == iblb::MK_SHELL;
+}
+
+}  // namespace
+
 struct iblb_batch {
   std::vector<iblb_ctx *> inst;
   std::vector<cudaStream_t> streams;  // one per instance (the instance's own stream)
   std::vector<cudaEvent_t> joins;     // one per instance
   cudaStream_t stream = nullptr;      // caller's stream
-  cudaStream_t cap = nullptr;         // origin stream of the graph capture
-  cudaEvent_t fork = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  std::vector<uint64_t> gens;  // config_gen, cur, map of every instance when captured
+  iblb::Ctx part;                     // the batch's SM partitions and their streams (ib, ls)
+  cudaEvent_t ev_force = nullptr, ev_coll = nullptr, ev_join = nullptr;
+  std::vector<Group> groups;
+  std::vector<Table> tabs;     // [parity][group][kernel]
+  void *arena = nullptr;       // device: every table's records and block offsets
+  bool tables = false;         // tabs/arena hold records of the instances' current state
+  std::vector<uint64_t> gens;  // config_gen, cur, map of every instance when recorded
   std::vector<int> curs, maps;
   std::vector<int> status;     // per-instance result of the last iblb_batch_step
   int *health = nullptr;       // pinned, one word per instance
@@ -32,8 +68,6 @@ struct iblb_batch {
 };
 
 namespace {
-
-constexpr int kGraphSteps = 2;  // even: the double buffers are back in place after a replay
 
 int bfail(iblb_batch *b, int code, const std::string &msg) {
   b->err = msg;
@@ -58,8 +92,8 @@ cudaError_t follow(cudaStream_t to, cudaStream_t from, cudaEvent_t ev) {
   return e == cudaSuccess ? cudaStreamWaitEvent(to, ev, 0) : e;
 }
 
-bool graph_current(const iblb_batch *b) {
-  if (!b->exec) return false;
+bool tables_current(const iblb_batch *b) {
+  if (!b->tables) return false;
   for (size_t i = 0; i < b->inst.size(); i++) {
     const Ctx &c = b->inst[i]->c;
     if (b->gens[i] != c.config_gen || b->curs[i] != c.cur || b->maps[i] != c.map) return false;
@@ -67,53 +101,129 @@ bool graph_current(const iblb_batch *b) {
   return true;
 }
 
-// Capture kGraphSteps steps of every instance into b->exec. Queuing a step advances the host
-// copy of a context's state (buffer indices, counters), so that state is put back afterwards:
-// the graph has been recorded, nothing has run.
-int capture(iblb_batch *b) {
-  if (b->exec) {
-    cudaGraphExecDestroy(b->exec);
-    b->exec = nullptr;
+std::vector<Group> make_groups(const iblb_batch *b) {
+  std::map<int, std::vector<int>> by_precision;
+  for (size_t i = 0; i < b->inst.size(); i++)
+    by_precision[b->inst[i]->c.precision].push_back((int)i);
+  std::vector<Group> groups;
+  for (const auto &kv : by_precision)
+    for (size_t o = 0; o < kv.second.size(); o += iblb::kMultiMax) {
+      Group g;
+      g.precision = kv.first;
+      const size_t e = std::min(kv.second.size(), o + (size_t)iblb::kMultiMax);
+      g.members.assign(kv.second.begin() + o, kv.second.begin() + e);
+      groups.push_back(g);
+    }
+  return groups;
+}
+
+// Build the argument records and block tables of every batched launch, for both parities of a
+// pair of steps from the instances' current state, into one device arena.
+int build_tables(iblb_batch *b) {
+  if (b->arena) {
+    BATCH_TRY(b, cudaStreamSynchronize(b->stream));  // the last steps that read it are done
+    cudaFree(b->arena);
+    b->arena = nullptr;
   }
-  BATCH_TRY(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  b->tables = false;
+  b->groups = make_groups(b);
+  const size_t G = b->groups.size(), n = b->inst.size();
+  b->tabs.assign(kPairSteps * G * kNumKernels, Table());
+  std::vector<int> cur0(n), map0(n);
+  for (size_t i = 0; i < n; i++) {
+    cur0[i] = b->inst[i]->c.cur;
+    map0[i] = b->inst[i]->c.map;
+  }
   int rc = 0;
-  if (cudaEventRecord(b->fork, b->cap) != cudaSuccess) rc = bfail(b, IBLB_ECUDA, "capture fork");
-  for (size_t i = 0; i < b->inst.size() && rc == 0; i++) {
-    Ctx &c = b->inst[i]->c;
-    const int cur = c.cur, map = c.map, fresh = c.fresh, have_force = c.have_force;
-    const int64_t steps = c.steps_done, k1l = c.k1_launches, kl = c.kernel_launches;
-    if (cudaStreamWaitEvent(c.stream, b->fork, 0) != cudaSuccess) rc = IBLB_ECUDA;
-    if (rc == 0) rc = iblb::enqueue_steps(c, kGraphSteps);
-    if (rc == 0 && cudaEventRecord(b->joins[i], c.stream) != cudaSuccess) rc = IBLB_ECUDA;
-    if (rc == 0 && cudaStreamWaitEvent(b->cap, b->joins[i], 0) != cudaSuccess) rc = IBLB_ECUDA;
-    c.cur = cur;
-    c.map = map;
-    c.fresh = fresh;
-    c.have_force = have_force;
-    c.steps_done = steps;
-    c.k1_launches = k1l;
-    c.kernel_launches = kl;
-    if (rc) rc = inst_fail(b, (int)i, rc);
+  for (int p = 0; p < kPairSteps && rc == 0; p++) {
+    for (size_t i = 0; i < n; i++) {  // the state a step of this parity starts from
+      Ctx &c = b->inst[i]->c;
+      c.cur = cur0[i] ^ p;
+      c.map = map0[i] ^ (c.nv ? p : 0);
+    }
+    for (size_t g = 0; g < G && rc == 0; g++)
+      for (int ki = 0; ki < kNumKernels && rc == 0; ki++) {
+        Table &t = b->tabs[(p * G + g) * kNumKernels + ki];
+        const MultiKernel k = kKernels[ki];
+        for (int i : b->groups[g].members) {
+          const Ctx &c = b->inst[i]->c;
+          if (k != iblb::MK_STREAM_COLLIDE && c.nv == 0) continue;  // no mesh: lattice only
+          const int blocks = lattice_kernel(k) ? iblb::lattice_multi_record(c, k, t.bytes)
+                                               : iblb::ib_multi_record(c, k, t.bytes);
+          if (blocks < 1) {
+            rc = bfail(b, IBLB_ECUDA, "batched launch without a record");
+            break;
+          }
+          t.start.push_back(t.start.back() + blocks);
+        }
+      }
   }
-  cudaGraph_t graph = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
-  if (rc) {
-    if (graph) cudaGraphDestroy(graph);
-    return rc;
+  for (size_t i = 0; i < n; i++) {
+    b->inst[i]->c.cur = cur0[i];
+    b->inst[i]->c.map = map0[i];
   }
-  if (e != cudaSuccess) return bfail(b, IBLB_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  const cudaError_t e2 = cudaGraphInstantiate(&b->exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e2 != cudaSuccess) {
-    b->exec = nullptr;
-    return bfail(b, IBLB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+  if (rc) return rc;
+  // each table's records, then its block offsets, each 256-byte aligned (a multiple of every
+  // record's alignment)
+  size_t total = 0;
+  for (Table &t : b->tabs) {
+    t.args_off = total;
+    total = (total + t.bytes.size() + 255) / 256 * 256;
+    t.start_off = total;
+    total = (total + t.start.size() * sizeof(int) + 255) / 256 * 256;
   }
-  for (size_t i = 0; i < b->inst.size(); i++) {
+  std::vector<unsigned char> image(total, 0);
+  for (const Table &t : b->tabs) {
+    if (!t.bytes.empty()) memcpy(image.data() + t.args_off, t.bytes.data(), t.bytes.size());
+    memcpy(image.data() + t.start_off, t.start.data(), t.start.size() * sizeof(int));
+  }
+  BATCH_TRY(b, cudaMalloc(&b->arena, total));
+  BATCH_TRY(b, cudaMemcpy(b->arena, image.data(), total, cudaMemcpyHostToDevice));
+  for (size_t i = 0; i < n; i++) {
     const Ctx &c = b->inst[i]->c;
     b->gens[i] = c.config_gen;
     b->curs[i] = c.cur;
     b->maps[i] = c.map;
   }
+  b->tables = true;
+  return 0;
+}
+
+// Queue kernel ki of every group (records of step parity p) on stream s.
+int launch_kernel(iblb_batch *b, int p, int ki, cudaStream_t s) {
+  const size_t G = b->groups.size();
+  for (size_t g = 0; g < G; g++) {
+    const Table &t = b->tabs[(p * G + g) * kNumKernels + ki];
+    iblb::MultiLaunch m;
+    m.n = (int)t.start.size() - 1;
+    if (m.n == 0) continue;
+    m.blocks = t.start.back();
+    m.args = (const unsigned char *)b->arena + t.args_off;
+    m.start = (const int *)((const unsigned char *)b->arena + t.start_off);
+    const MultiKernel k = kKernels[ki];
+    const cudaError_t e = lattice_kernel(k) ? iblb::lattice_launch_multi(b->groups[g].precision, k, m, s)
+                                            : iblb::ib_launch_multi(b->groups[g].precision, k, m, s);
+    if (e != cudaSuccess)
+      return bfail(b, IBLB_ECUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+  }
+  return 0;
+}
+
+// Queue one coupled step of every instance (records of parity p): the interface chain on the
+// interface stream, the stream-collide passes on the lattice stream, joined by events as in
+// iblb_step.
+int enqueue_batched_step(iblb_batch *b, int p) {
+  cudaStream_t ifc = b->part.ib, lat = b->part.ls;
+  for (int ki = 0; ki < 4; ki++)  // K3a, K3b, K4a, K4b
+    if (int rc = launch_kernel(b, p, ki, ifc)) return rc;
+  BATCH_TRY(b, cudaEventRecord(b->ev_force, ifc));
+  if (int rc = launch_kernel(b, p, 4, lat)) return rc;  // K1
+  BATCH_TRY(b, cudaStreamWaitEvent(lat, b->ev_force, 0));
+  if (int rc = launch_kernel(b, p, 5, lat)) return rc;  // K1t
+  BATCH_TRY(b, cudaEventRecord(b->ev_coll, lat));
+  BATCH_TRY(b, cudaStreamWaitEvent(ifc, b->ev_coll, 0));
+  for (int ki = 6; ki < 8; ki++)  // K1b, K2
+    if (int rc = launch_kernel(b, p, ki, ifc)) return rc;
   return 0;
 }
 
@@ -129,8 +239,20 @@ int iblb_batch_create(const iblb_lattice_desc *descs, int32_t n, void *cuda_stre
   iblb_batch *b = new iblb_batch();
   b->stream = (cudaStream_t)cuda_stream;
   int rc = 0;
-  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  // two streams, the interface chain's and the lattice passes'; with descs[0].ib_sms > 0 they
+  // run on SM partitions as a single context's. The default is no partition: the interface
+  // work of many meshes needs more SMs than the lattice pass can leave it (96 wetting boxes:
+  // 14.1k MLUPS with 32 interface SMs, 19.0k with 48, 23.0k with 64 or with no partition)
+  int prio_lo = 0, prio_hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  const int want = descs[0].ib_sms;
+  if (e == cudaSuccess && !(want > 0 && iblb::split_sms(b->part, want, prio_hi))) {
+    e = cudaStreamCreateWithFlags(&b->part.ib, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->part.ls, cudaStreamNonBlocking);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_force, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_coll, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->health, sizeof(int) * n);
   for (int i = 0; i < n && e == cudaSuccess && rc == 0; i++) {
     cudaStream_t s = nullptr;
@@ -163,12 +285,21 @@ int iblb_batch_create(const iblb_lattice_desc *descs, int32_t n, void *cuda_stre
 void iblb_batch_destroy(iblb_batch *b) {
   if (!b) return;
   for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
+  cudaStreamSynchronize(b->stream);
+  if (b->part.ib) cudaStreamSynchronize(b->part.ib);
+  if (b->part.ls) cudaStreamSynchronize(b->part.ls);
+  if (b->arena) cudaFree(b->arena);
   for (iblb_ctx *h : b->inst) iblb_destroy(h);
   for (cudaEvent_t ev : b->joins) cudaEventDestroy(ev);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
-  if (b->fork) cudaEventDestroy(b->fork);
-  if (b->cap) cudaStreamDestroy(b->cap);
+  for (cudaEvent_t ev : {b->ev_force, b->ev_coll, b->ev_join})
+    if (ev) cudaEventDestroy(ev);
+  if (b->part.green[0]) {
+    iblb::release_sms(b->part);
+  } else {
+    if (b->part.ib) cudaStreamDestroy(b->part.ib);
+    if (b->part.ls) cudaStreamDestroy(b->part.ls);
+  }
   if (b->health) cudaFreeHost(b->health);
   delete b;
 }
@@ -256,19 +387,25 @@ int iblb_batch_step(iblb_batch *b, int32_t nsteps) {
       if (int rc = iblb::enqueue_steps(b->inst[i]->c, 1)) return inst_fail(b, (int)i, rc);
     done = 1;
   }
-  if (nsteps - done >= kGraphSteps) {
-    if (!graph_current(b))
-      if (int rc = capture(b)) return rc;
+  if (nsteps - done >= kPairSteps) {
+    if (!tables_current(b))
+      if (int rc = build_tables(b)) return rc;
+    // the partition streams start after everything queued on the instances' streams
     for (size_t i = 0; i < n; i++) BATCH_TRY(b, follow(b->stream, b->inst[i]->c.stream, b->joins[i]));
-    for (; nsteps - done >= kGraphSteps; done += kGraphSteps) {
-      BATCH_TRY(b, cudaGraphLaunch(b->exec, b->stream));
+    BATCH_TRY(b, follow(b->part.ib, b->stream, b->ev_join));
+    BATCH_TRY(b, follow(b->part.ls, b->stream, b->ev_join));
+    for (; nsteps - done >= kPairSteps; done += kPairSteps) {
+      for (int p = 0; p < kPairSteps; p++)
+        if (int rc = enqueue_batched_step(b, p)) return rc;
       for (size_t i = 0; i < n; i++) {
         Ctx &c = b->inst[i]->c;
-        c.steps_done += kGraphSteps;
+        c.steps_done += kPairSteps;
         if (c.nv) c.have_force = 1;
         c.fresh = 0;
       }
     }
+    BATCH_TRY(b, follow(b->stream, b->part.ib, b->ev_join));
+    BATCH_TRY(b, follow(b->stream, b->part.ls, b->ev_join));
     for (size_t i = 0; i < n; i++) BATCH_TRY(b, follow(b->inst[i]->c.stream, b->stream, b->joins[i]));
   }
   if (nsteps > done)

@@ -6,6 +6,7 @@
 // Arithmetic runs in the population type `real` (float or double); vertex positions, the
 // enclosed volume V and V - V0 are always double.
 #include <math.h>
+#include <string.h>
 
 #include "iblb_internal.cuh"
 
@@ -75,15 +76,37 @@ struct FaceParams {
 // a sum of terms proportional to the displacement, so float arithmetic loses nothing to the
 // cancellation between V and V0 (the per-block partials are summed in double).
 template <typename real>
-__global__ void __launch_bounds__(256) face_kernel(
-    int nf, const int *__restrict__ faces, const Vec4<real> *__restrict__ disp,
-    const double *__restrict__ fref, const real *__restrict__ fgeo,
-    real *__restrict__ fcontrib, real *__restrict__ fnorm,
-    double *__restrict__ vol_partial, FaceParams fp, Dims D, int *__restrict__ other_tile_slot,
-    const int *__restrict__ other_slot_tile, const int *__restrict__ other_nslots, int reset,
-    int *__restrict__ ovf_count) {
+struct FaceArgs {
+  int nf;
+  const int *faces;
+  const Vec4<real> *disp;
+  const double *fref;
+  const real *fgeo;
+  real *fcontrib, *fnorm;
+  double *vol_partial;
+  FaceParams fp;
+  Dims D;
+  int *other_tile_slot;
+  const int *other_slot_tile, *other_nslots;
+  int reset;
+  int *ovf_count;
+};
+
+// K3a for block `bid` of `nb` (the single-context kernel and the batched one share it).
+template <typename real>
+__device__ __forceinline__ void face_body(const FaceArgs<real> &A, int bid, int nb) {
+  const int nf = A.nf;
+  const int *__restrict__ faces = A.faces;
+  const Vec4<real> *__restrict__ disp = A.disp;
+  const double *__restrict__ fref = A.fref;
+  const real *__restrict__ fgeo = A.fgeo;
+  real *__restrict__ fcontrib = A.fcontrib;
+  real *__restrict__ fnorm = A.fnorm;
+  double *__restrict__ vol_partial = A.vol_partial;
+  const FaceParams fp = A.fp;
+  const Dims D = A.D;
   __shared__ double warp_sum[8];
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = bid * blockDim.x + threadIdx.x;
   real dvj = 0;
   if (j < nf) {
     const int iv[3] = {faces[3 * j], faces[3 * j + 1], faces[3 * j + 2]};
@@ -167,17 +190,29 @@ __global__ void __launch_bounds__(256) face_kernel(
   if (threadIdx.x < 32) {
     double v = threadIdx.x < (blockDim.x >> 5) ? warp_sum[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) vol_partial[blockIdx.x] = v;
+    if (threadIdx.x == 0) vol_partial[bid] = v;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ovf_count[0] = 0;  // overflow list length
-    ovf_count[2] = 0;  // number of source tiles (counters[4])
+  if (bid == 0 && threadIdx.x == 0) {
+    A.ovf_count[0] = 0;  // overflow list length
+    A.ovf_count[2] = 0;  // number of source tiles (counters[4])
   }
-  if (reset) {
-    const int n_other = min(*other_nslots, D.max_slots);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_other; s += gridDim.x * blockDim.x)
-      other_tile_slot[other_slot_tile[s]] = -1;
+  if (A.reset) {
+    const int n_other = min(*A.other_nslots, D.max_slots);
+    for (int s = bid * blockDim.x + threadIdx.x; s < n_other; s += nb * blockDim.x)
+      A.other_tile_slot[A.other_slot_tile[s]] = -1;
   }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) face_kernel(const FaceArgs<real> A) {
+  face_body(A, blockIdx.x, gridDim.x);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) face_kernel_multi(const FaceArgs<real> *__restrict__ all,
+                                                         const int *__restrict__ start, int n) {
+  const MultiBlock m = multi_block(start, n);
+  face_body(all[m.inst], m.block, m.nblocks);
 }
 
 // kV (V - V0)/V0 from the per-block partial sums of V - V0, by one warp in a fixed order;
@@ -216,16 +251,31 @@ constexpr int GATHER_UNROLL = 8;
 // after V is complete. Then the delta stencil of the vertex and its binning into the source
 // tile (the tile that holds its base node).
 template <typename real>
-__global__ void __launch_bounds__(256) vertex_kernel(
-    int nv, const int *__restrict__ vf_start, const int *__restrict__ vf_list,
-    const real *__restrict__ fcontrib, const real *__restrict__ fnorm,
-    const double *__restrict__ q, Vec4<real> *__restrict__ phi, Vec4<real> *__restrict__ gvol,
-    StencilRec<real> *__restrict__ stencil, int bin, const int *__restrict__ tile_slot,
-    int *__restrict__ slot_count, int *__restrict__ bucket, int *__restrict__ overflow,
-    int *__restrict__ ovf_count, int *__restrict__ src_index, int *__restrict__ nsources,
-    int *__restrict__ health, int *__restrict__ zero_counter, Dims D) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && zero_counter) *zero_counter = 0;
+struct VertexArgs {
+  int nv;
+  const int *vf_start, *vf_list;
+  const real *fcontrib, *fnorm;
+  const double *q;
+  Vec4<real> *phi, *gvol;
+  StencilRec<real> *stencil;
+  int bin;
+  const int *tile_slot;
+  int *slot_count, *bucket, *overflow, *ovf_count, *src_index, *nsources, *health, *zero_counter;
+  Dims D;
+};
+
+template <typename real>
+__device__ __forceinline__ void vertex_body(const VertexArgs<real> &A, int bid) {
+  const int nv = A.nv;
+  const int *__restrict__ vf_start = A.vf_start;
+  const int *__restrict__ vf_list = A.vf_list;
+  const real *__restrict__ fcontrib = A.fcontrib;
+  const real *__restrict__ fnorm = A.fnorm;
+  const double *__restrict__ q = A.q;
+  const int bin = A.bin;
+  const Dims D = A.D;
+  const int i = bid * blockDim.x + threadIdx.x;
+  if (bid == 0 && threadIdx.x == 0 && A.zero_counter) *A.zero_counter = 0;
   if (i >= nv) return;
   const int e0 = vf_start[i], e1 = vf_start[i + 1];
   real F[3] = {0, 0, 0}, g[3] = {0, 0, 0};
@@ -247,8 +297,8 @@ __global__ void __launch_bounds__(256) vertex_kernel(
   Vec4<real> pv, gv;
   pv.x = F[0]; pv.y = F[1]; pv.z = F[2]; pv.w = real(0);
   gv.x = g[0]; gv.y = g[1]; gv.z = g[2]; gv.w = real(0);
-  phi[i] = pv;
-  gvol[i] = gv;
+  A.phi[i] = pv;
+  A.gvol[i] = gv;
   if (!bin) return;
   StencilRec<real> rec;
   peskin_weights<real>(wrap_pos(q[3 * (size_t)i], D.nx, D.inx), rec.base[0], rec.w[0]);
@@ -260,22 +310,34 @@ __global__ void __launch_bounds__(256) vertex_kernel(
   if (rec.base[1] < 0) rec.base[1] += D.ny;
   if (!D.has_walls && rec.base[2] < 0) rec.base[2] += D.nz;
   rec.pad = 0;
-  stencil[i] = rec;
+  A.stencil[i] = rec;
   const int bz = min(max(rec.base[2], 0), D.nz - 1);
   const int t = ((bz >> 2) * D.nty + (rec.base[1] >> 2)) * D.ntx + (rec.base[0] >> 2);
-  const int s = tile_slot[t];
+  const int s = A.tile_slot[t];
   if (s < 0) {
-    atomicOr(health, H_CAPACITY);
+    atomicOr(A.health, H_CAPACITY);
     return;
   }
-  const int rank = atomicAdd(&slot_count[s], 1);
-  if (rank == 0) src_index[s] = atomicAdd(nsources, 1);  // first vertex: the tile gets a region
+  const int rank = atomicAdd(&A.slot_count[s], 1);
+  if (rank == 0) A.src_index[s] = atomicAdd(A.nsources, 1);  // first vertex: the tile gets a region
   if (rank < BUCKET_CAP) {
-    bucket[(size_t)s * BUCKET_CAP + rank] = i;
+    A.bucket[(size_t)s * BUCKET_CAP + rank] = i;
   } else {
-    const int o = atomicAdd(ovf_count, 1);
-    overflow[o] = i;
+    const int o = atomicAdd(A.ovf_count, 1);
+    A.overflow[o] = i;
   }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) vertex_kernel(const VertexArgs<real> A) {
+  vertex_body(A, blockIdx.x);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) vertex_kernel_multi(
+    const VertexArgs<real> *__restrict__ all, const int *__restrict__ start, int n) {
+  const MultiBlock m = multi_block(start, n);
+  vertex_body(all[m.inst], m.block);
 }
 
 struct VolumeParams {
@@ -308,30 +370,49 @@ __device__ __forceinline__ real pick4(const real w[4], int d) {
 // Vertices in the overflow list (more than 64 in a tile) follow in list order. The order of
 // summation is fixed by the sorted buckets.
 template <typename real>
-__global__ void __launch_bounds__(32 * SrcWarps<real>::value) spread_source_kernel(
-    const int *__restrict__ tile_slot, const int *__restrict__ slot_tile,
-    const int *__restrict__ nslots_ptr, const int *__restrict__ slot_count,
-    const int *__restrict__ src_index, const int *__restrict__ bucket,
-    const int *__restrict__ overflow, const int *__restrict__ ovf_count_ptr,
-    const StencilRec<real> *__restrict__ stencil, const Vec4<real> *__restrict__ phi,
-    const Vec4<real> *__restrict__ gvol, const double *__restrict__ vol_partial, VolumeParams vp,
-    int *__restrict__ health, Vec4<real> *__restrict__ Rslot, int *__restrict__ out_src, Dims D) {
+struct SourceArgs {
+  const int *tile_slot, *slot_tile, *nslots_ptr, *slot_count, *src_index, *bucket, *overflow,
+      *ovf_count_ptr;
+  const StencilRec<real> *stencil;
+  const Vec4<real> *phi, *gvol;
+  const double *vol_partial;
+  VolumeParams vp;
+  int *health;
+  Vec4<real> *Rslot;
+  int *out_src;
+  Dims D;
+};
+
+template <typename real>
+__device__ __forceinline__ void spread_source_body(const SourceArgs<real> &A, int bid, int nb) {
+  const int *__restrict__ tile_slot = A.tile_slot;
+  const int *__restrict__ slot_tile = A.slot_tile;
+  const int *__restrict__ slot_count = A.slot_count;
+  const int *__restrict__ src_index = A.src_index;
+  const int *__restrict__ bucket = A.bucket;
+  const int *__restrict__ overflow = A.overflow;
+  const StencilRec<real> *__restrict__ stencil = A.stencil;
+  const Vec4<real> *__restrict__ phi = A.phi;
+  const Vec4<real> *__restrict__ gvol = A.gvol;
+  const VolumeParams vp = A.vp;
+  int *__restrict__ out_src = A.out_src;
+  const Dims D = A.D;
   constexpr int W = SrcWarps<real>::value;
   __shared__ Vec4<real> s_region[W][REGION_NODES];
   __shared__ real s_w[W][BUCKET_CAP][12];
   __shared__ Vec4<real> s_f[W][BUCKET_CAP];
   __shared__ int s_b[W][BUCKET_CAP][3];
-  const int nslots = min(*nslots_ptr, D.max_slots);
-  const int novf = *ovf_count_ptr;
+  const int nslots = min(*A.nslots_ptr, D.max_slots);
+  const int novf = *A.ovf_count_ptr;
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   double V;
-  const real coef = (real)volume_coef(vol_partial, vp.vol_blocks, vp.V0, vp.kV, vp.volume_on, &V);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && !(fabs(V / vp.V0 - 1.0) <= 0.05))
-    atomicOr(health, H_VOLUME);
+  const real coef = (real)volume_coef(A.vol_partial, vp.vol_blocks, vp.V0, vp.kV, vp.volume_on, &V);
+  if (bid == 0 && threadIdx.x == 0 && !(fabs(V / vp.V0 - 1.0) <= 0.05))
+    atomicOr(A.health, H_VOLUME);
   Vec4<real> *region = s_region[wq];
   // the two stencil nodes of this lane
   const int dxa = lane & 3, dya = (lane >> 2) & 3, dza = lane >> 4;  // node lane; node lane + 32
-  for (int s = blockIdx.x * W + wq; s < nslots; s += gridDim.x * W) {
+  for (int s = bid * W + wq; s < nslots; s += nb * W) {
     const int cnt = slot_count[s];
     if (cnt == 0) continue;  // no vertex has its base node here: no region
     const int n = min(cnt, BUCKET_CAP);
@@ -421,10 +502,23 @@ __global__ void __launch_bounds__(32 * SrcWarps<real>::value) spread_source_kern
       }
       __syncwarp();
     }
-    Vec4<real> *out = Rslot + (size_t)reg * REGION_NODES;
+    Vec4<real> *out = A.Rslot + (size_t)reg * REGION_NODES;
     for (int k = lane; k < REGION_NODES; k += 32) out[k] = region[k];
     __syncwarp();
   }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(32 * SrcWarps<real>::value) spread_source_kernel(
+    const SourceArgs<real> A) {
+  spread_source_body(A, blockIdx.x, gridDim.x);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(32 * SrcWarps<real>::value) spread_source_kernel_multi(
+    const SourceArgs<real> *__restrict__ all, const int *__restrict__ start, int n) {
+  const MultiBlock m = multi_block(start, n);
+  spread_source_body(all[m.inst], m.block, m.nblocks);
 }
 
 // K4b: spreading, second pass. One 64-thread block per active tile T (grid-stride), thread =
@@ -433,14 +527,24 @@ __global__ void __launch_bounds__(32 * SrcWarps<real>::value) spread_source_kern
 // periodic axis only 4 nodes long S - e and S coincide and the two terms are the node's two
 // images in the region. Force landing on a wall layer is dropped.
 template <typename real>
-__global__ void __launch_bounds__(64) spread_gather_kernel(
-    const int *__restrict__ slot_tile, const int *__restrict__ nslots_ptr,
-    const int *__restrict__ out_src, const Vec4<real> *__restrict__ Rslot,
-    Vec4<real> *__restrict__ Fslot, Dims D) {
-  const int nslots = min(*nslots_ptr, D.max_slots);
+struct GatherArgs {
+  const int *slot_tile, *nslots_ptr, *out_src;
+  const Vec4<real> *Rslot;
+  Vec4<real> *Fslot;
+  Dims D;
+};
+
+template <typename real>
+__device__ __forceinline__ void spread_gather_body(const GatherArgs<real> &A, int bid, int nb) {
+  const int *__restrict__ slot_tile = A.slot_tile;
+  const int *__restrict__ out_src = A.out_src;
+  const Vec4<real> *__restrict__ Rslot = A.Rslot;
+  Vec4<real> *__restrict__ Fslot = A.Fslot;
+  const Dims D = A.D;
+  const int nslots = min(*A.nslots_ptr, D.max_slots);
   const int tid = threadIdx.x;
   const int lx = tid & 3, ly = (tid >> 2) & 3, lz = tid >> 4;
-  for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
+  for (int b = bid; b < nslots; b += nb) {
     const int *src = out_src + 8 * (size_t)b;
     real f[3] = {0, 0, 0};
     for (int e = 0; e < 8; e++) {
@@ -461,6 +565,18 @@ __global__ void __launch_bounds__(64) spread_gather_kernel(
     o.w = real(0);
     Fslot[(size_t)b * TILE_CELLS + tid] = o;
   }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(64) spread_gather_kernel(const GatherArgs<real> A) {
+  spread_gather_body(A, blockIdx.x, gridDim.x);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(64) spread_gather_kernel_multi(
+    const GatherArgs<real> *__restrict__ all, const int *__restrict__ start, int n) {
+  const MultiBlock m = multi_block(start, n);
+  spread_gather_body(all[m.inst], m.block, m.nblocks);
 }
 
 // Claim tile t in map (tile_slot, slot_tile, nslots): the first claimant takes a new slot.
@@ -531,14 +647,34 @@ __device__ __forceinline__ void mark_tile(const AxisTiles ax[3], int e, const Di
 // the update is added to the double position. Each lane then marks two of the (up to 8)
 // tiles of the new position in the other map.
 template <typename real>
-__global__ void __launch_bounds__(256) interp_kernel(
-    int nv, const StencilRec<real> *__restrict__ stencil, const int *__restrict__ tile_slot,
-    const Vec4<real> *__restrict__ Uslot, double *__restrict__ q, double *__restrict__ qdot,
-    const double *__restrict__ xref, Vec4<real> *__restrict__ disp,
-    double3 ub, double3 ut, Dims D, int *__restrict__ next_tile_slot,
-    int *__restrict__ next_slot_tile, int *__restrict__ next_nslots, int *__restrict__ slot_count,
-    int *__restrict__ out_src, int *__restrict__ health) {
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+struct InterpArgs {
+  int nv;
+  const StencilRec<real> *stencil;
+  const int *tile_slot;
+  const Vec4<real> *Uslot;
+  double *q, *qdot;
+  const double *xref;
+  Vec4<real> *disp;
+  double3 ub, ut;
+  Dims D;
+  int *next_tile_slot, *next_slot_tile, *next_nslots, *slot_count, *out_src, *health;
+};
+
+template <typename real>
+__device__ __forceinline__ void interp_body(const InterpArgs<real> &A, int bid) {
+  const int nv = A.nv;
+  const StencilRec<real> *__restrict__ stencil = A.stencil;
+  const int *__restrict__ tile_slot = A.tile_slot;
+  const Vec4<real> *__restrict__ Uslot = A.Uslot;
+  double *__restrict__ q = A.q;
+  double *__restrict__ qdot = A.qdot;
+  const double *__restrict__ xref = A.xref;
+  Vec4<real> *__restrict__ disp = A.disp;
+  const double3 ub = A.ub, ut = A.ut;
+  const Dims D = A.D;
+  int *next_tile_slot = A.next_tile_slot;
+  int *__restrict__ health = A.health;
+  const int gid = bid * blockDim.x + threadIdx.x;
   const int v = gid >> 2;
   const int dz = gid & 3;
   const bool valid = v < nv;
@@ -621,12 +757,24 @@ __global__ void __launch_bounds__(256) interp_kernel(
       ax[0] = axis_tiles(pn[0], D.ntx, D.inx, true);
       ax[1] = axis_tiles(pn[1], D.nty, D.iny, true);
       ax[2] = axis_tiles(pn[2], D.ntz, D.inz, !D.has_walls);
-      mark_tile(ax, dz, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, out_src,
-                health);
-      mark_tile(ax, dz + 4, D, next_tile_slot, next_slot_tile, next_nslots, slot_count, out_src,
-                health);
+      mark_tile(ax, dz, D, next_tile_slot, A.next_slot_tile, A.next_nslots, A.slot_count,
+                A.out_src, health);
+      mark_tile(ax, dz + 4, D, next_tile_slot, A.next_slot_tile, A.next_nslots, A.slot_count,
+                A.out_src, health);
     }
   }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) interp_kernel(const InterpArgs<real> A) {
+  interp_body(A, blockIdx.x);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) interp_kernel_multi(
+    const InterpArgs<real> *__restrict__ all, const int *__restrict__ start, int n) {
+  const MultiBlock m = multi_block(start, n);
+  interp_body(all[m.inst], m.block);
 }
 
 // Standalone marking of the current positions (after setting vertices); also refreshes the
@@ -724,69 +872,243 @@ VolumeParams volume_params(const Ctx &c) {
   return vp;
 }
 
+// Argument records of the step kernels for context c as it is now (its cur and map), shared by
+// the single-context launches and the batched ones.
+template <typename real>
+FaceArgs<real> face_args(const Ctx &c, int reset) {
+  FaceArgs<real> a;
+  a.fp.a1 = c.iface.alpha[0];
+  a.fp.a2 = c.iface.alpha[1];
+  a.fp.a3 = c.iface.alpha[2];
+  a.fp.eps48 = 48.0 * c.iface.eps;
+  a.fp.xi = c.iface.xi;
+  a.fp.wall_on = c.iface.wall_force_on;
+  const int other = c.map ^ 1;
+  a.nf = c.nf;
+  a.faces = c.faces;
+  a.disp = (const Vec4<real> *)c.disp;
+  a.fref = c.fref;
+  a.fgeo = (const real *)c.fgeo;
+  a.fcontrib = (real *)c.fcontrib;
+  a.fnorm = (real *)c.fnorm;
+  a.vol_partial = c.vol_partial;
+  a.D = dims_of(c);
+  a.other_tile_slot = c.tile_slot[other];
+  a.other_slot_tile = c.slot_tile[other];
+  a.other_nslots = c.counters + other;
+  a.reset = reset;
+  a.ovf_count = c.counters + 2;
+  return a;
+}
+int face_blocks(const Ctx &c) { return c.vol_blocks; }
+
+template <typename real>
+VertexArgs<real> vertex_args(const Ctx &c, int bin) {
+  VertexArgs<real> a;
+  a.nv = c.nv;
+  a.vf_start = c.vf_start;
+  a.vf_list = c.vf_list;
+  a.fcontrib = (const real *)c.fcontrib;
+  a.fnorm = (const real *)c.fnorm;
+  a.q = c.q;
+  a.phi = (Vec4<real> *)c.phi;
+  a.gvol = (Vec4<real> *)c.gvol;
+  a.stencil = (StencilRec<real> *)c.stencil;
+  a.bin = bin;
+  a.tile_slot = c.tile_slot[c.map];
+  a.slot_count = c.slot_count;
+  a.bucket = c.bucket;
+  a.overflow = c.overflow;
+  a.ovf_count = c.counters + 2;
+  a.src_index = c.src_index;
+  a.nsources = c.counters + 4;
+  a.health = c.counters + 3;
+  a.zero_counter = bin == 2 ? c.counters + (c.map ^ 1) : nullptr;
+  a.D = dims_of(c);
+  return a;
+}
+int vertex_blocks(const Ctx &c) { return (c.nv + 255) / 256; }
+
+template <typename real>
+SourceArgs<real> source_args(const Ctx &c) {
+  SourceArgs<real> a;
+  a.tile_slot = c.tile_slot[c.map];
+  a.slot_tile = c.slot_tile[c.map];
+  a.nslots_ptr = c.counters + c.map;
+  a.slot_count = c.slot_count;
+  a.src_index = c.src_index;
+  a.bucket = c.bucket;
+  a.overflow = c.overflow;
+  a.ovf_count_ptr = c.counters + 2;
+  a.stencil = (const StencilRec<real> *)c.stencil;
+  a.phi = (const Vec4<real> *)c.phi;
+  a.gvol = (const Vec4<real> *)c.gvol;
+  a.vol_partial = c.vol_partial;
+  a.vp = volume_params(c);
+  a.health = c.counters + 3;
+  a.Rslot = (Vec4<real> *)c.Rslot;
+  a.out_src = c.out_src[c.map];
+  a.D = dims_of(c);
+  return a;
+}
+// persistent grids sized to the SMs the interface chain runs on; in a batch (no partition,
+// many contexts side by side) to the context's expected active tiles instead: one warp per
+// two (source) tiles
+template <typename real>
+int source_blocks(const Ctx &c, bool batched) {
+  constexpr int W = SrcWarps<real>::value;
+  const int sms = c.ib_sms > 0 ? c.ib_sms : c.sm_count;
+  int g = batched ? (c.tile_estimate + 2 * W - 1) / (2 * W) : sms * 8;
+  if (g * W > c.max_slots) g = (c.max_slots + W - 1) / W;
+  return g < 1 ? 1 : g;
+}
+
+template <typename real>
+GatherArgs<real> gather_args(const Ctx &c) {
+  GatherArgs<real> a;
+  a.slot_tile = c.slot_tile[c.map];
+  a.nslots_ptr = c.counters + c.map;
+  a.out_src = c.out_src[c.map];
+  a.Rslot = (const Vec4<real> *)c.Rslot;
+  a.Fslot = (Vec4<real> *)c.Fslot[c.map];
+  a.D = dims_of(c);
+  return a;
+}
+int gather_blocks(const Ctx &c, bool batched) {
+  const int sms = c.ib_sms > 0 ? c.ib_sms : c.sm_count;
+  int g = batched ? (c.tile_estimate + 1) / 2 : sms * 16;  // batched: a block per two tiles
+  if (g > c.max_slots) g = c.max_slots;
+  return g < 1 ? 1 : g;
+}
+
+template <typename real>
+InterpArgs<real> interp_args(const Ctx &c) {
+  const int other = c.map ^ 1;
+  InterpArgs<real> a;
+  a.nv = c.nv;
+  a.stencil = (const StencilRec<real> *)c.stencil;
+  a.tile_slot = c.tile_slot[c.map];
+  a.Uslot = (const Vec4<real> *)c.Uslot;
+  a.q = c.q;
+  a.qdot = c.qdot;
+  a.xref = c.xref;
+  a.disp = (Vec4<real> *)c.disp;
+  a.ub = make_double3(c.ub[0], c.ub[1], c.ub[2]);
+  a.ut = make_double3(c.ut[0], c.ut[1], c.ut[2]);
+  a.D = dims_of(c);
+  a.next_tile_slot = c.tile_slot[other];
+  a.next_slot_tile = c.slot_tile[other];
+  a.next_nslots = c.counters + other;
+  a.slot_count = c.slot_count;
+  a.out_src = c.out_src[other];
+  a.health = c.counters + 3;
+  return a;
+}
+int interp_blocks(const Ctx &c) { return (int)((4L * c.nv + 255) / 256); }
+
 template <typename real>
 cudaError_t face_forces_t(Ctx &c, int reset, cudaStream_t st) {
-  FaceParams fp;
-  fp.a1 = c.iface.alpha[0];
-  fp.a2 = c.iface.alpha[1];
-  fp.a3 = c.iface.alpha[2];
-  fp.eps48 = 48.0 * c.iface.eps;
-  fp.xi = c.iface.xi;
-  fp.wall_on = c.iface.wall_force_on;
-  const int other = c.map ^ 1;
-  face_kernel<real><<<c.vol_blocks, 256, 0, st>>>(
-      c.nf, c.faces, (const Vec4<real> *)c.disp, c.fref, (const real *)c.fgeo,
-      (real *)c.fcontrib, (real *)c.fnorm, c.vol_partial, fp, dims_of(c), c.tile_slot[other],
-      c.slot_tile[other],
-      c.counters + other, reset, c.counters + 2);
+  face_kernel<real><<<face_blocks(c), 256, 0, st>>>(face_args<real>(c, reset));
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t vertex_forces_t(Ctx &c, int bin, cudaStream_t st) {
-  vertex_kernel<real><<<(c.nv + 255) / 256, 256, 0, st>>>(
-      c.nv, c.vf_start, c.vf_list, (const real *)c.fcontrib, (const real *)c.fnorm, c.q,
-      (Vec4<real> *)c.phi, (Vec4<real> *)c.gvol, (StencilRec<real> *)c.stencil, bin, c.tile_slot[c.map],
-      c.slot_count, c.bucket, c.overflow, c.counters + 2, c.src_index, c.counters + 4,
-      c.counters + 3, bin == 2 ? c.counters + (c.map ^ 1) : nullptr, dims_of(c));
+  vertex_kernel<real><<<vertex_blocks(c), 256, 0, st>>>(vertex_args<real>(c, bin));
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t spread_t(Ctx &c, cudaStream_t st) {
-  // persistent grids sized to the SMs the interface chain runs on
   constexpr int W = SrcWarps<real>::value;
-  const int sms = c.ib_sms > 0 ? c.ib_sms : c.sm_count;
-  int g1 = sms * 8;
-  if (g1 * W > c.max_slots) g1 = (c.max_slots + W - 1) / W;
-  spread_source_kernel<real><<<g1 < 1 ? 1 : g1, 32 * W, 0, st>>>(
-      c.tile_slot[c.map], c.slot_tile[c.map], c.counters + c.map, c.slot_count, c.src_index,
-      c.bucket, c.overflow, c.counters + 2, (const StencilRec<real> *)c.stencil,
-      (const Vec4<real> *)c.phi, (const Vec4<real> *)c.gvol, c.vol_partial, volume_params(c),
-      c.counters + 3, (Vec4<real> *)c.Rslot, c.out_src[c.map], dims_of(c));
+  spread_source_kernel<real><<<source_blocks<real>(c, false), 32 * W, 0, st>>>(source_args<real>(c));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int g2 = sms * 16;
-  if (g2 > c.max_slots) g2 = c.max_slots;
-  spread_gather_kernel<real><<<g2 < 1 ? 1 : g2, TILE_CELLS, 0, st>>>(
-      c.slot_tile[c.map], c.counters + c.map, c.out_src[c.map], (const Vec4<real> *)c.Rslot,
-      (Vec4<real> *)c.Fslot[c.map], dims_of(c));
+  spread_gather_kernel<real><<<gather_blocks(c, false), TILE_CELLS, 0, st>>>(gather_args<real>(c));
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t interp_t(Ctx &c, cudaStream_t st) {
-  const int other = c.map ^ 1;
-  const long threads = 4L * c.nv;
-  interp_kernel<real><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-      c.nv, (const StencilRec<real> *)c.stencil, c.tile_slot[c.map], (const Vec4<real> *)c.Uslot,
-      c.q, c.qdot, c.xref, (Vec4<real> *)c.disp, make_double3(c.ub[0], c.ub[1], c.ub[2]),
-      make_double3(c.ut[0], c.ut[1], c.ut[2]), dims_of(c), c.tile_slot[other],
-      c.slot_tile[other], c.counters + other, c.slot_count, c.out_src[other], c.counters + 3);
+  interp_kernel<real><<<interp_blocks(c), 256, 0, st>>>(interp_args<real>(c));
   return cudaGetLastError();
 }
 
+template <typename T>
+void append_record(std::vector<unsigned char> &bytes, const T &rec) {
+  const size_t off = bytes.size();
+  bytes.resize(off + sizeof(T));
+  memcpy(bytes.data() + off, &rec, sizeof(T));
+}
+
+template <typename real>
+int ib_multi_record_t(const Ctx &c, MultiKernel k, std::vector<unsigned char> &bytes) {
+  switch (k) {
+    case MK_FACE: append_record(bytes, face_args<real>(c, 1)); return face_blocks(c);
+    case MK_VERTEX: append_record(bytes, vertex_args<real>(c, 2)); return vertex_blocks(c);
+    case MK_SOURCE: append_record(bytes, source_args<real>(c)); return source_blocks<real>(c, true);
+    case MK_GATHER: append_record(bytes, gather_args<real>(c)); return gather_blocks(c, true);
+    case MK_INTERP: append_record(bytes, interp_args<real>(c)); return interp_blocks(c);
+    default: return -1;
+  }
+}
+
+template <typename real>
+cudaError_t ib_launch_multi_t(MultiKernel k, const MultiLaunch &m, cudaStream_t s) {
+  constexpr int W = SrcWarps<real>::value;
+  switch (k) {
+    case MK_FACE:
+      face_kernel_multi<real><<<m.blocks, 256, 0, s>>>((const FaceArgs<real> *)m.args, m.start, m.n);
+      break;
+    case MK_VERTEX:
+      vertex_kernel_multi<real><<<m.blocks, 256, 0, s>>>((const VertexArgs<real> *)m.args, m.start,
+                                                          m.n);
+      break;
+    case MK_SOURCE:
+      spread_source_kernel_multi<real><<<m.blocks, 32 * W, 0, s>>>(
+          (const SourceArgs<real> *)m.args, m.start, m.n);
+      break;
+    case MK_GATHER:
+      spread_gather_kernel_multi<real><<<m.blocks, TILE_CELLS, 0, s>>>(
+          (const GatherArgs<real> *)m.args, m.start, m.n);
+      break;
+    case MK_INTERP:
+      interp_kernel_multi<real><<<m.blocks, 256, 0, s>>>((const InterpArgs<real> *)m.args, m.start,
+                                                          m.n);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename real>
+size_t ib_record_align(MultiKernel k) {
+  switch (k) {
+    case MK_FACE: return alignof(FaceArgs<real>);
+    case MK_VERTEX: return alignof(VertexArgs<real>);
+    case MK_SOURCE: return alignof(SourceArgs<real>);
+    case MK_GATHER: return alignof(GatherArgs<real>);
+    case MK_INTERP: return alignof(InterpArgs<real>);
+    default: return 0;
+  }
+}
+
 }  // namespace
+
+int ib_multi_record(const Ctx &c, MultiKernel k, std::vector<unsigned char> &bytes) {
+  return c.precision == IBLB_FP64 ? ib_multi_record_t<double>(c, k, bytes)
+                                  : ib_multi_record_t<float>(c, k, bytes);
+}
+
+cudaError_t ib_launch_multi(int precision, MultiKernel k, const MultiLaunch &m, cudaStream_t s) {
+  return precision == IBLB_FP64 ? ib_launch_multi_t<double>(k, m, s)
+                                : ib_launch_multi_t<float>(k, m, s);
+}
+
+size_t ib_multi_record_align(int precision, MultiKernel k) {
+  return precision == IBLB_FP64 ? ib_record_align<double>(k) : ib_record_align<float>(k);
+}
 
 size_t stencil_record_bytes(const Ctx &c) {
   return c.precision == IBLB_FP64 ? sizeof(StencilRec<double>) : sizeof(StencilRec<float>);

@@ -51,6 +51,35 @@ constexpr int kStages = 4, kStageWarps = 8;
 // Default size of one population's copy in the staged pass (bytes): rows per unit follow.
 constexpr size_t kStageCopyBytes = 4096;
 
+// Batched launches: one grid over the blocks of many contexts. Instance i of a launch owns the
+// grid's blocks start[i] .. start[i + 1] - 1 (start[0] = 0, start[n] = the grid size).
+constexpr int kMultiMax = 256;  // instances per batched launch
+
+struct MultiBlock {
+  int inst;     // instance of this block
+  int block;    // block index within the instance's share
+  int nblocks;  // blocks of the instance
+};
+
+// Instance and local block of this block (every thread of the block must call it).
+__device__ __forceinline__ MultiBlock multi_block(const int *__restrict__ start, int n) {
+  __shared__ int s_start[kMultiMax + 1];
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) s_start[k] = start[k];
+  __syncthreads();
+  const int b = blockIdx.x;
+  int lo = 0, hi = n;  // the largest lo with start[lo] <= b
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (s_start[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  MultiBlock m;
+  m.inst = lo;
+  m.block = b - s_start[lo];
+  m.nblocks = s_start[lo + 1] - s_start[lo];
+  return m;
+}
+
 // Force and velocity blocks of the active tiles are [slot][64 nodes] of these: x, y, z and one
 // pad, so that each node is one aligned vector access.
 template <typename real>
@@ -91,6 +120,7 @@ struct Ctx {
   int ntx = 0, nty = 0, ntz = 0;
   size_t ntiles = 0;
   int max_slots = 0;
+  int tile_estimate = 0;  // active tiles expected for the mesh (sizes the batched grids)
   int *tile_slot[2] = {nullptr, nullptr};  // [ntiles] slot or -1
   int *slot_tile[2] = {nullptr, nullptr};  // [max_slots] tile id of each active slot
   int *counters = nullptr;  // [0..1] nslots per map, [2] overflow count, [3] health, [4] sources
@@ -138,7 +168,7 @@ struct Ctx {
   size_t dscratch_len = 0;
   int sm_count = 0;
   int k1_rows = 0;          // lattice rows per block of the stream-collide pass (0: 1)
-  int k1_kind = 0;          // IBLB_STREAM_COLLIDE_STAGED or IBLB_STREAM_COLLIDE_DIRECT
+  int k1_kind = 0;          // IBLB_STREAM_COLLIDE_AUTO, _STAGED or _DIRECT
   int k1_stages = 0;        // stages of the staged pass (0: kStages)
   int k1_warps = 0;         // compute warps per block of the staged pass (0: kStageWarps)
   int k1_unit_rows = 0;     // lattice rows per unit of the staged pass (0: by copy size)
@@ -148,6 +178,12 @@ struct Ctx {
   std::string err;
 };
 
+// Split the device's SMs into an interface partition of about `want` SMs and a lattice
+// partition with the rest (green contexts), setting c.green, c.ib (interface stream, priority
+// prio_hi), c.ls, c.ib_sms and c.lat_sms; false (nothing created) where the device or driver
+// cannot partition. release_sms undoes it.
+bool split_sms(Ctx &c, int want, int prio_hi);
+void release_sms(Ctx &c);
 // Queue nsteps coupled steps on the context's streams: no synchronisation, no health read
 // (iblb_step adds those). Returns 0 or an IBLB_E* code (message in c.err).
 int enqueue_steps(Ctx &c, int nsteps);
@@ -185,6 +221,37 @@ cudaError_t launch_clear_counts(Ctx &c);
 cudaError_t launch_expand_force(Ctx &c, double *F_dev);
 cudaError_t launch_phi_to_double(Ctx &c, double *phi_dev);
 cudaError_t launch_volume(Ctx &c, double *V_dev);
+
+// Batched step kernels: each covers a group of contexts of one precision in one launch (the
+// batched ensemble). A record is the argument block one context's kernel would be launched
+// with, for the context's current buffer indices (cur, map).
+enum MultiKernel {
+  MK_FACE,            // K3a
+  MK_VERTEX,          // K3b
+  MK_SOURCE,          // K4a
+  MK_GATHER,          // K4b
+  MK_STREAM_COLLIDE,  // K1 (not the first, in-place step)
+  MK_TILES,           // K1t
+  MK_SHELL,           // K1b
+  MK_INTERP,          // K2
+};
+struct MultiLaunch {
+  const void *args = nullptr;  // device: the n records, one per context
+  const int *start = nullptr;  // device: n + 1 block offsets
+  int n = 0, blocks = 0;
+};
+// Append context c's record for kernel k to `bytes` and return its number of blocks (at least
+// 1), or -1 where k does not belong to this file.
+int ib_multi_record(const Ctx &c, MultiKernel k, std::vector<unsigned char> &bytes);
+int lattice_multi_record(const Ctx &c, MultiKernel k, std::vector<unsigned char> &bytes);
+// Alignment of the records of kernel k for this precision (records are packed at their size);
+// 0 where k does not belong to the file.
+size_t ib_multi_record_align(int precision, MultiKernel k);
+size_t lattice_multi_record_align(int precision, MultiKernel k);
+// Launch kernel k over the records of m (contexts of precision `precision`) on stream s.
+cudaError_t ib_launch_multi(int precision, MultiKernel k, const MultiLaunch &m, cudaStream_t s);
+cudaError_t lattice_launch_multi(int precision, MultiKernel k, const MultiLaunch &m,
+                                 cudaStream_t s);
 
 }  // namespace iblb
 

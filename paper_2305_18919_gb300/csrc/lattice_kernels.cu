@@ -10,6 +10,7 @@
 // arithmetic type `real` (FP16 / BF16 storage with FP32 arithmetic), see Storage below.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <string.h>
 
 #include "iblb_internal.cuh"
 
@@ -455,15 +456,9 @@ __device__ __forceinline__ unsigned int as_bits(V2 v) {
 // nodes x0, x0 + 1, `hi` nodes x0 + 2, x0 + 3) and are widened one node pair at a time for
 // the collision; the results are packed back in place.
 template <typename S, bool FIRST, bool FORCE>
-__global__ void __launch_bounds__(128) stream_collide_quad_kernel(const S *__restrict__ fin,
-                                                                  S *__restrict__ fout,
-                                                                  const LatParams<float> P,
-                                                                  int z0) {
+__device__ __forceinline__ void quad_nodes(const S *__restrict__ fin, S *__restrict__ fout,
+                                           const LatParams<float> &P, int x0, int y, int z) {
   using V2 = typename Storage<S>::V2;
-  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;  // blockDim.y rows per block
-  const int z = blockIdx.z + z0;
-  if (x0 >= P.nx) return;
   const size_t plane = (size_t)P.nx * P.ny;
   const size_t n = (size_t)z * plane + (size_t)y * P.nx + x0;
   unsigned int lo[Q], hi[Q];  // packed pairs (x0, x0 + 1) and (x0 + 2, x0 + 3)
@@ -534,6 +529,18 @@ __global__ void __launch_bounds__(128) stream_collide_quad_kernel(const S *__res
 #pragma unroll
   for (int i = 0; i < Q; i++)
     *reinterpret_cast<uint2 *>(fout + (size_t)i * P.ncell + n) = make_uint2(lo[i], hi[i]);
+}
+
+template <typename S, bool FIRST, bool FORCE>
+__global__ void __launch_bounds__(128) stream_collide_quad_kernel(const S *__restrict__ fin,
+                                                                  S *__restrict__ fout,
+                                                                  const LatParams<float> P,
+                                                                  int z0) {
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;  // blockDim.y rows per block
+  const int z = blockIdx.z + z0;
+  if (x0 >= P.nx) return;
+  quad_nodes<S, FIRST, FORCE>(fin, fout, P, x0, y, z);
 }
 
 // --- K1s: stream-collide with the pulled rows staged in shared memory by bulk copies ----------
@@ -888,22 +895,78 @@ __global__ void __launch_bounds__(288, 1) stream_collide_staged_kernel(
   }
 }
 
+// K1 over many contexts in one launch (the batched ensemble; never the first, in-place step):
+// each thread takes one node group in memory order, a pair (x0, x0 + 1) or, with 16-bit
+// storage, four nodes x0 .. x0 + 3, and runs the very code of the single-context kernels on it,
+// so each context's populations come out bit for bit as from those.
+template <typename real, typename S>
+struct StreamArgs {
+  const S *fin;
+  S *fout;
+  LatParams<real> P;
+  int z0;       // first fluid layer
+  int per_row;  // node groups per lattice row
+  int ngroups;  // node groups of the context
+  int force;    // the body force is non-zero
+};
+
+template <typename real, typename S>
+__global__ void __launch_bounds__(128) stream_collide_kernel_multi(
+    const StreamArgs<real, S> *__restrict__ all, const int *__restrict__ start, int n) {
+  const MultiBlock m = multi_block(start, n);
+  const StreamArgs<real, S> &A = all[m.inst];
+  const int g = m.block * blockDim.x + threadIdx.x;
+  if (g >= A.ngroups) return;
+  const int row = g / A.per_row;
+  const int y = row % A.P.ny, z = A.z0 + row / A.P.ny;
+  if constexpr (sizeof(S) == 2) {
+    const int x0 = 4 * (g - row * A.per_row);
+    if (A.force) quad_nodes<S, false, true>(A.fin, A.fout, A.P, x0, y, z);
+    else quad_nodes<S, false, false>(A.fin, A.fout, A.P, x0, y, z);
+  } else {
+    const int x0 = 2 * (g - row * A.per_row);
+    real a[Q], b[Q];
+    load_pair<real, S, false>(A.fin, A.P, x0, y, z, a, b);
+    const real F[3] = {A.P.g[0], A.P.g[1], A.P.g[2]};
+    if (A.force) {
+      collide<real, true>(a, F, A.P);
+      collide<real, true>(b, F, A.P);
+    } else {
+      collide<real, false>(a, F, A.P);
+      collide<real, false>(b, F, A.P);
+    }
+    store_pair(A.fout, A.P, (size_t)z * A.P.nx * A.P.ny + (size_t)y * A.P.nx + x0, a, b);
+  }
+}
+
 // K1t: stream-collide of the fluid nodes of the active tiles with body + interface force,
 // one warp per tile (grid-stride), each thread the node pair (x0, x0 + 1) of a tile row as in
 // K1. Runs after K1 of the same step and overwrites those nodes. Pairs whose interface force
 // is zero keep K1's result, which is already the post-collision state with the body force
 // alone.
+template <typename real, typename S>
+struct TilesArgs {
+  const S *fin;
+  S *fout;
+  const int *slot_tile, *nslots_ptr;
+  const Vec4<real> *Fslot;
+  LatParams<real> P;
+  int max_slots;
+};
+
 template <typename real, typename S, bool FIRST>
-__global__ void __launch_bounds__(128) stream_collide_tiles_kernel(
-    const S *__restrict__ fin, S *__restrict__ fout, const int *__restrict__ slot_tile,
-    const int *__restrict__ nslots_ptr, const Vec4<real> *__restrict__ Fslot,
-    const LatParams<real> P, int max_slots) {
-  const int nslots = min(*nslots_ptr, max_slots);
+__device__ __forceinline__ void tiles_body(const TilesArgs<real, S> &A, int bid, int nb) {
+  const S *__restrict__ fin = A.fin;
+  S *__restrict__ fout = A.fout;
+  const int *__restrict__ slot_tile = A.slot_tile;
+  const Vec4<real> *__restrict__ Fslot = A.Fslot;
+  const LatParams<real> P = A.P;  // held in registers: the loop below is latency-bound
+  const int nslots = min(*A.nslots_ptr, A.max_slots);
   const int lane = threadIdx.x & 31;
   const int px = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
   const int cell = 16 * lz + 4 * ly + 2 * px;
   const int warps = blockDim.x >> 5;
-  for (int s = blockIdx.x * warps + (threadIdx.x >> 5); s < nslots; s += gridDim.x * warps) {
+  for (int s = bid * warps + (threadIdx.x >> 5); s < nslots; s += nb * warps) {
     const Vec4<real> Fa = Fslot[(size_t)s * TILE_CELLS + cell];
     const Vec4<real> Fb = Fslot[(size_t)s * TILE_CELLS + cell + 1];
     const int t = slot_tile[s];
@@ -923,20 +986,42 @@ __global__ void __launch_bounds__(128) stream_collide_tiles_kernel(
   }
 }
 
+template <typename real, typename S, bool FIRST>
+__global__ void __launch_bounds__(128) stream_collide_tiles_kernel(const TilesArgs<real, S> A) {
+  tiles_body<real, S, FIRST>(A, blockIdx.x, gridDim.x);
+}
+
+template <typename real, typename S>
+__global__ void __launch_bounds__(128) stream_collide_tiles_kernel_multi(
+    const TilesArgs<real, S> *__restrict__ all, const int *__restrict__ start, int n) {
+  const MultiBlock m = multi_block(start, n);
+  tiles_body<real, S, false>(all[m.inst], m.block, m.nblocks);
+}
+
 // K1b: velocity after streaming at every node of the active interface tiles.
 // One 64-thread block per active tile (grid-stride over the device-side tile count).
 template <typename real, typename S>
-__global__ void __launch_bounds__(64) shell_velocity_kernel(const S *__restrict__ fpost,
-                                                            const int *__restrict__ slot_tile,
-                                                            const int *__restrict__ nslots_ptr,
-                                                            const Vec4<real> *__restrict__ Fslot,
-                                                            Vec4<real> *__restrict__ Uslot,
-                                                            const LatParams<real> P, real ubx,
-                                                            real uby, real ubz, real utx,
-                                                            real uty, real utz, int max_slots) {
-  const int nslots = min(*nslots_ptr, max_slots);
+struct ShellArgs {
+  const S *fpost;
+  const int *slot_tile, *nslots_ptr;
+  const Vec4<real> *Fslot;
+  Vec4<real> *Uslot;
+  LatParams<real> P;
+  real ubx, uby, ubz, utx, uty, utz;
+  int max_slots;
+};
+
+template <typename real, typename S>
+__device__ __forceinline__ void shell_body(const ShellArgs<real, S> &A, int bid, int nb) {
+  const S *__restrict__ fpost = A.fpost;
+  const int *__restrict__ slot_tile = A.slot_tile;
+  const Vec4<real> *__restrict__ Fslot = A.Fslot;
+  Vec4<real> *__restrict__ Uslot = A.Uslot;
+  const LatParams<real> P = A.P;
+  const real ubx = A.ubx, uby = A.uby, ubz = A.ubz, utx = A.utx, uty = A.uty, utz = A.utz;
+  const int nslots = min(*A.nslots_ptr, A.max_slots);
   const int cell = threadIdx.x;
-  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+  for (int s = bid; s < nslots; s += nb) {
     const int t = slot_tile[s];
     const int tx = t % P.ntx, ty = (t / P.ntx) % P.nty, tz = t / (P.ntx * P.nty);
     const int x = tx * TILE + (cell & 3), y = ty * TILE + ((cell >> 2) & 3),
@@ -975,6 +1060,18 @@ __global__ void __launch_bounds__(64) shell_velocity_kernel(const S *__restrict_
     uv.w = real(0);
     Uslot[(size_t)s * TILE_CELLS + cell] = uv;
   }
+}
+
+template <typename real, typename S>
+__global__ void __launch_bounds__(64) shell_velocity_kernel(const ShellArgs<real, S> A) {
+  shell_body<real, S>(A, blockIdx.x, gridDim.x);
+}
+
+template <typename real, typename S>
+__global__ void __launch_bounds__(64) shell_velocity_kernel_multi(
+    const ShellArgs<real, S> *__restrict__ all, const int *__restrict__ start, int n) {
+  const MultiBlock m = multi_block(start, n);
+  shell_body<real, S>(all[m.inst], m.block, m.nblocks);
 }
 
 // rho and u of every node of the current post-streaming state (read-back, not on the step).
@@ -1192,36 +1289,135 @@ cudaError_t stream_collide_t(Ctx &c, int first, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Argument records of K1t and K1b for the step that starts from c's current state (K1t pulls
+// from f[cur] into f[cur ^ 1]; K1b reads the array that step writes, `fpost`).
+template <typename real, typename S>
+TilesArgs<real, S> tiles_args(const Ctx &c) {
+  TilesArgs<real, S> a;
+  a.fin = (const S *)c.f[c.cur];
+  a.fout = (S *)c.f[c.cur ^ 1];
+  a.slot_tile = c.slot_tile[c.map];
+  a.nslots_ptr = c.counters + c.map;
+  a.Fslot = (const Vec4<real> *)c.Fslot[c.map];
+  a.P = lat_params<real>(c);
+  a.max_slots = c.max_slots;
+  return a;
+}
+// 4 tiles per block; single context: up to ~4900 active tiles in one pass; in a batch one
+// warp per two of the context's expected active tiles
+int tiles_blocks(const Ctx &c, bool batched) {
+  int grid = batched ? (c.tile_estimate + 7) / 8 : c.sm_count * 8;
+  if (4 * grid > c.max_slots) grid = (c.max_slots + 3) / 4;
+  return grid < 1 ? 1 : grid;
+}
+
+template <typename real, typename S>
+ShellArgs<real, S> shell_args(const Ctx &c, const void *fpost) {
+  ShellArgs<real, S> a;
+  a.fpost = (const S *)fpost;
+  a.slot_tile = c.slot_tile[c.map];
+  a.nslots_ptr = c.counters + c.map;
+  a.Fslot = (const Vec4<real> *)c.Fslot[c.map];
+  a.Uslot = (Vec4<real> *)c.Uslot;
+  a.P = lat_params<real>(c);
+  a.ubx = (real)c.ub[0];
+  a.uby = (real)c.ub[1];
+  a.ubz = (real)c.ub[2];
+  a.utx = (real)c.ut[0];
+  a.uty = (real)c.ut[1];
+  a.utz = (real)c.ut[2];
+  a.max_slots = c.max_slots;
+  return a;
+}
+int shell_blocks(const Ctx &c, bool batched) {
+  int grid = batched ? (c.tile_estimate + 1) / 2 : c.sm_count * 32;  // batched: per two tiles
+  if (grid > c.max_slots) grid = c.max_slots;
+  return grid < 1 ? 1 : grid;
+}
+
+template <typename real, typename S>
+StreamArgs<real, S> stream_args(const Ctx &c) {
+  StreamArgs<real, S> a;
+  a.fin = (const S *)c.f[c.cur];
+  a.fout = (S *)c.f[c.cur ^ 1];
+  a.P = lat_params<real>(c);
+  a.z0 = c.has_walls ? 1 : 0;
+  a.per_row = sizeof(S) == 2 ? c.nx / 4 : c.nx / 2;
+  a.ngroups = a.per_row * c.ny * (c.has_walls ? c.nz - 2 : c.nz);
+  a.force = c.g[0] != 0.0 || c.g[1] != 0.0 || c.g[2] != 0.0;
+  return a;
+}
+
 template <typename real, typename S>
 cudaError_t stream_collide_tiles_t(Ctx &c, int first, cudaStream_t st) {
-  const LatParams<real> P = lat_params<real>(c);
-  int grid = c.sm_count * 8;  // 4 tiles per block: up to ~4900 active tiles in one pass
-  if (4 * grid > c.max_slots) grid = (c.max_slots + 3) / 4;
-  if (grid < 1) grid = 1;
-  const S *fin = (const S *)c.f[c.cur];
-  S *fout = (S *)c.f[c.cur ^ 1];
+  const int grid = tiles_blocks(c, false);
   if (first)
-    stream_collide_tiles_kernel<real, S, true><<<grid, 128, 0, st>>>(
-        fin, fout, c.slot_tile[c.map], c.counters + c.map, (const Vec4<real> *)c.Fslot[c.map], P,
-        c.max_slots);
+    stream_collide_tiles_kernel<real, S, true><<<grid, 128, 0, st>>>(tiles_args<real, S>(c));
   else
-    stream_collide_tiles_kernel<real, S, false><<<grid, 128, 0, st>>>(
-        fin, fout, c.slot_tile[c.map], c.counters + c.map, (const Vec4<real> *)c.Fslot[c.map], P,
-        c.max_slots);
+    stream_collide_tiles_kernel<real, S, false><<<grid, 128, 0, st>>>(tiles_args<real, S>(c));
   return cudaGetLastError();
 }
 
 template <typename real, typename S>
 cudaError_t shell_velocity_t(Ctx &c, cudaStream_t st) {
-  const LatParams<real> P = lat_params<real>(c);
-  int grid = c.sm_count * 32;
-  if (grid > c.max_slots) grid = c.max_slots;
-  if (grid < 1) grid = 1;
-  shell_velocity_kernel<real, S><<<grid, TILE_CELLS, 0, st>>>(
-      (const S *)c.f[c.cur], c.slot_tile[c.map], c.counters + c.map,
-      (const Vec4<real> *)c.Fslot[c.map], (Vec4<real> *)c.Uslot, P, (real)c.ub[0], (real)c.ub[1], (real)c.ub[2], (real)c.ut[0],
-      (real)c.ut[1], (real)c.ut[2], c.max_slots);
+  shell_velocity_kernel<real, S><<<shell_blocks(c, false), TILE_CELLS, 0, st>>>(
+      shell_args<real, S>(c, c.f[c.cur]));
   return cudaGetLastError();
+}
+
+template <typename T>
+void append_record(std::vector<unsigned char> &bytes, const T &rec) {
+  const size_t off = bytes.size();
+  bytes.resize(off + sizeof(T));
+  memcpy(bytes.data() + off, &rec, sizeof(T));
+}
+
+template <typename real, typename S>
+int lattice_multi_record_t(const Ctx &c, MultiKernel k, std::vector<unsigned char> &bytes) {
+  switch (k) {
+    case MK_STREAM_COLLIDE: {
+      const StreamArgs<real, S> a = stream_args<real, S>(c);
+      append_record(bytes, a);
+      const int b = (a.ngroups + 127) / 128;
+      return b < 1 ? 1 : b;
+    }
+    case MK_TILES: append_record(bytes, tiles_args<real, S>(c)); return tiles_blocks(c, true);
+    case MK_SHELL:
+      append_record(bytes, shell_args<real, S>(c, c.f[c.cur ^ 1]));
+      return shell_blocks(c, true);
+    default: return -1;
+  }
+}
+
+template <typename real, typename S>
+cudaError_t lattice_launch_multi_t(MultiKernel k, const MultiLaunch &m, cudaStream_t s) {
+  switch (k) {
+    case MK_STREAM_COLLIDE:
+      stream_collide_kernel_multi<real, S><<<m.blocks, 128, 0, s>>>(
+          (const StreamArgs<real, S> *)m.args, m.start, m.n);
+      break;
+    case MK_TILES:
+      stream_collide_tiles_kernel_multi<real, S><<<m.blocks, 128, 0, s>>>(
+          (const TilesArgs<real, S> *)m.args, m.start, m.n);
+      break;
+    case MK_SHELL:
+      shell_velocity_kernel_multi<real, S><<<m.blocks, TILE_CELLS, 0, s>>>(
+          (const ShellArgs<real, S> *)m.args, m.start, m.n);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename real, typename S>
+size_t lattice_record_align_t(MultiKernel k) {
+  switch (k) {
+    case MK_STREAM_COLLIDE: return alignof(StreamArgs<real, S>);
+    case MK_TILES: return alignof(TilesArgs<real, S>);
+    case MK_SHELL: return alignof(ShellArgs<real, S>);
+    default: return 0;
+  }
 }
 
 template <typename real, typename S>
@@ -1276,6 +1472,29 @@ int k1_block_rows(const Ctx &c) {
   }
 
 bool stream_collide_staged(const Ctx &c) { IBLB_DISPATCH(c, uses_staged_t, c) }
+
+int lattice_multi_record(const Ctx &c, MultiKernel k, std::vector<unsigned char> &bytes) {
+  IBLB_DISPATCH(c, lattice_multi_record_t, c, k, bytes)
+}
+
+cudaError_t lattice_launch_multi(int precision, MultiKernel k, const MultiLaunch &m,
+                                 cudaStream_t s) {
+  switch (precision) {
+    case IBLB_FP64: return lattice_launch_multi_t<double, double>(k, m, s);
+    case IBLB_FP16: return lattice_launch_multi_t<float, __half>(k, m, s);
+    case IBLB_BF16: return lattice_launch_multi_t<float, __nv_bfloat16>(k, m, s);
+    default: return lattice_launch_multi_t<float, float>(k, m, s);
+  }
+}
+
+size_t lattice_multi_record_align(int precision, MultiKernel k) {
+  switch (precision) {
+    case IBLB_FP64: return lattice_record_align_t<double, double>(k);
+    case IBLB_FP16: return lattice_record_align_t<float, __half>(k);
+    case IBLB_BF16: return lattice_record_align_t<float, __nv_bfloat16>(k);
+    default: return lattice_record_align_t<float, float>(k);
+  }
+}
 
 cudaError_t launch_stream_collide(Ctx &c, int first, cudaStream_t s) {
   IBLB_DISPATCH(c, stream_collide_t, c, first, s)

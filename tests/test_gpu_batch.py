@@ -106,3 +106,51 @@ def test_failing_instance_is_reported_by_index():
     assert e.value.code == binding.IBLB_EUNSTABLE
     assert list(b.status()) == [0, 0, binding.IBLB_EUNSTABLE]
     b.close()
+
+
+def test_lattice_only_instances_beside_meshes():
+    """Contexts without a mesh take only the stream-collide launches of the batched step;
+    they and the mesh contexts beside them end as when stepped alone."""
+    from paper_2305_18919_gb300 import binding
+    wls = _small_ensemble()
+    descs = [binding.workload_desc(wl, "fp32") for wl in wls]
+    descs.insert(1, binding.lattice_desc(16, 12, 10, 0.9, 1.0, (-0.01, 0, 0), (0.02, 0, 0),
+                                         (1e-5, 0, 0), "fp32", False, -1))
+    b = binding.Batch(descs)
+    meshed = [b.contexts[0], b.contexts[2], b.contexts[3]]
+    for lat, wl in zip(meshed, wls):
+        v, f = wl.mesh()
+        lat.add_mesh(v, f)
+        lat.set_interface(wl.alpha, wl.kV, wl.eps, wl.xi, wl.wall_force_on, wl.volume_force_on)
+    b.step(6)
+    assert list(b.status()) == [0, 0, 0, 0]
+    for lat, wl in zip(meshed, wls):
+        _same(lat, _alone(wl, "fp32", [6]))
+    ref = binding.Lattice(16, 12, 10, 0.9, 1.0, (-0.01, 0, 0), (0.02, 0, 0), (1e-5, 0, 0),
+                          "fp32", False, None, -1)
+    ref.step(6)
+    assert np.array_equal(b.contexts[1].populations(), ref.populations())
+    ref.close()
+    b.close()
+
+
+def test_more_instances_than_one_launch_holds():
+    """260 contexts of one precision: the batched launches split them into groups of at most
+    256; every context still ends as when stepped alone."""
+    from paper_2305_18919_gb300 import binding
+    rng = np.random.default_rng(4)
+    descs, ubs = [], []
+    for k in range(260):
+        ubs.append((float(rng.uniform(-0.02, 0.02)), 0.0, 0.0))
+        descs.append(binding.lattice_desc(8, 8, 6, 0.8, 1.0, ubs[k], (0, 0, 0), (0, 0, 0), "fp32",
+                                          False, -1))
+    b = binding.Batch(descs)
+    b.step(4)
+    assert all(s == 0 for s in b.status())
+    for k in (0, 255, 256, 259):
+        ref = binding.Lattice(8, 8, 6, 0.8, 1.0, ubs[k], (0, 0, 0), precision="fp32",
+                              ib_sms=-1)
+        ref.step(4)
+        assert np.array_equal(b.contexts[k].populations(), ref.populations())
+        ref.close()
+    b.close()
