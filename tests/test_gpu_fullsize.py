@@ -66,3 +66,34 @@ def test_full_size_mass_conservation():
     V, V0 = lat.volume()
     assert abs(V / V0 - 1) < 1e-3
     lat.close()
+
+
+@pytest.mark.parametrize("precision,kind", [("fp32", "direct"), ("fp16", "staged")])
+def test_beyond_32_bit_element_offsets(precision, kind):
+    """A 512 x 512 x 520 lattice: each population array holds 19 x 136 M = 2.6 G elements, past
+    2^31, so every element offset must be formed in 64 bits. Started from a state that repeats
+    in x and y with period 32, it must evolve bit for bit like the 32 x 32 x 520 lattice (whose
+    parity with the oracle the smaller tests check), at both ends of the big arrays."""
+    from paper_2305_18919_gb300 import binding
+    nz, p, n = 520, 32, 512
+    rng = np.random.default_rng(12)
+    rho = 1 + rng.uniform(-0.01, 0.01, (nz, p, p))
+    u = rng.uniform(-0.03, 0.03, (nz, p, p, 3))
+    walls = ((-0.02, 0.01, 0), (0.03, -0.01, 0))
+    small = binding.Lattice(p, p, nz, 0.8, 1.0, *walls, precision=precision)
+    small.set_stream_collide(kind)
+    small.init_equilibrium(rho, u)
+    small.step(3)
+    r_s, u_s = small.fields()
+    small.close()
+    big = binding.Lattice(n, n, nz, 0.8, 1.0, *walls, precision=precision)
+    assert big.stream_collide_staged() == (kind == "staged")
+    reps = (1, n // p, n // p)
+    big.init_equilibrium(np.tile(rho, reps), np.tile(u, reps + (1,)))
+    big.step(3)
+    r_b, u_b = big.fields()
+    big.close()
+    for ys, xs in ((slice(0, p), slice(0, p)), (slice(n - p, n), slice(n - p, n)),
+                   (slice(n - p, n), slice(0, p))):
+        assert np.array_equal(r_b[:, ys, xs], r_s)
+        assert np.array_equal(u_b[:, ys, xs], u_s)
