@@ -258,15 +258,17 @@ int iblb_adjoint_release(iblb_ctx *ctx);
    IBLB_STREAM_COLLIDE_AUTO (default): staged for 16-bit storage, direct otherwise (the faster
      of the two on GB300 for each storage type).
    Both kernels give the same populations bit for bit. stages: 0 (4) or 2..8, reduced to what
-   fits in shared memory; warps: 0 (8) or 1..8; rows: 0 (as many as keep one copy within 4 KB)
-   or a power of two up to 16 that divides ny. IBLB_EINVAL for anything else. A staged block
+   fits in shared memory; warps: 0 (8) or 1..16 (at most 8 with four nodes per lane); rows: 0
+   (as many as keep one copy within 4 KB) or a power of two up to 16 that divides ny; nodes:
+   nodes per compute lane with 16-bit storage, 0 (the default), 2 or 4 (FP32 always takes 2).
+   IBLB_EINVAL for anything else. A staged block
    whose wait for its copies gives up (after 1 s) returns early, and iblb_step then returns
    IBLB_ECUDA. */
 #define IBLB_STREAM_COLLIDE_AUTO 0
 #define IBLB_STREAM_COLLIDE_STAGED 1
 #define IBLB_STREAM_COLLIDE_DIRECT 2
 int iblb_set_stream_collide(iblb_ctx *ctx, int32_t kind, int32_t stages, int32_t warps,
-                            int32_t rows);
+                            int32_t rows, int32_t nodes);
 /* Limit in nanoseconds of each wait of the staged kernel's warps for a buffer to fill or to be
    released, on the GPU's global timer (default 1e9, range 0 .. 6e10; 0: a single non-blocking
    test, so that a block's first wait, which comes before its copies complete, gives up; this

@@ -84,7 +84,7 @@ SIGNATURES = {
     "iblb_profile": (_i32, [_vp, _dp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "iblb_bytes_per_cell": (_i64, [_vp]),
     "iblb_interface_sms": (_i32, [_vp]),
-    "iblb_set_stream_collide": (_i32, [_vp, _i32, _i32, _i32, _i32]),
+    "iblb_set_stream_collide": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),
     "iblb_stream_collide_staged": (_i32, [_vp]),
     "iblb_set_stage_wait_limit": (_i32, [_vp, _i64]),
     "iblb_mesh_volume_noalloc": (_i32, [_vp, _vp, _i32, _dp, _vp, _vp]),
@@ -337,14 +337,15 @@ class Lattice:
         """Whether the steps after the first take the staged stream-collide kernel."""
         return bool(self._L.iblb_stream_collide_staged(self.h))
 
-    def set_stream_collide(self, kind="auto", stages=0, warps=0, rows=0):
+    def set_stream_collide(self, kind="auto", stages=0, warps=0, rows=0, nodes=0):
         """Kernel of the stream-collide pass from the second step on: "staged" (population rows
         copied into shared memory by a producer warp: `stages` buffers, `warps` compute warps,
-        units of `rows` lattice rows; 0 for the defaults), "direct", or "auto" (staged for
-        16-bit storage) (iblb_set_stream_collide)."""
+        units of `rows` lattice rows, `nodes` per compute lane with 16-bit storage; 0 for the
+        defaults), "direct", or "auto" (staged for 16-bit storage) (iblb_set_stream_collide)."""
         k = {"auto": IBLB_STREAM_COLLIDE_AUTO, "staged": IBLB_STREAM_COLLIDE_STAGED,
              "direct": IBLB_STREAM_COLLIDE_DIRECT}[kind]
-        self._check(self._L.iblb_set_stream_collide(self.h, k, int(stages), int(warps), int(rows)))
+        self._check(self._L.iblb_set_stream_collide(self.h, k, int(stages), int(warps), int(rows),
+                                                    int(nodes)))
 
     # --- adjoint ---------------------------------------------------------------------
     def adjoint_record(self, nsteps, every=100):

@@ -824,7 +824,7 @@ int iblb_profile(iblb_ctx *h, double *k1_ms, int64_t *k1_launches, int64_t *kern
 }
 
 int iblb_set_stream_collide(iblb_ctx *h, int32_t kind, int32_t stages, int32_t warps,
-                            int32_t rows) {
+                            int32_t rows, int32_t nodes) {
   if (!h) return IBLB_EINVAL;
   Ctx &c = h->c;
   if (kind != IBLB_STREAM_COLLIDE_AUTO && kind != IBLB_STREAM_COLLIDE_STAGED &&
@@ -832,13 +832,15 @@ int iblb_set_stream_collide(iblb_ctx *h, int32_t kind, int32_t stages, int32_t w
     return fail(c, IBLB_EINVAL, "stream-collide kind must be AUTO (0), STAGED (1) or DIRECT (2)");
   if (stages != 0 && (stages < 2 || stages > 8))
     return fail(c, IBLB_EINVAL, "stages must be 0 or 2..8");
-  if (warps < 0 || warps > 8) return fail(c, IBLB_EINVAL, "warps must be 0 or 1..8");
+  if (nodes != 0 && nodes != 2 && nodes != 4) return fail(c, IBLB_EINVAL, "nodes must be 0, 2 or 4");
+  if (warps < 0 || warps > 16) return fail(c, IBLB_EINVAL, "warps must be 0 or 1..16");
   if (rows < 0 || rows > 16 || (rows & (rows - 1)) || (rows && c.ny % rows))
     return fail(c, IBLB_EINVAL, "rows must be 0 or a power of two up to 16 that divides ny");
   c.k1_kind = kind;
   c.k1_stages = stages;
   c.k1_warps = warps;
   c.k1_unit_rows = rows;
+  c.k1_nodes = nodes;
   c.config_gen++;
   return IBLB_OK;
 }

@@ -48,6 +48,8 @@ constexpr int H_TIMEOUT = 32;
 
 // Default shape of the staged stream-collide pass: stages per block, compute warps per block.
 constexpr int kStages = 4, kStageWarps = 8;
+// Nodes per compute lane of the staged pass with 16-bit storage (2 or 4).
+constexpr int kStageNodes16 = 4;
 // Default size of one population's copy in the staged pass (bytes): rows per unit follow.
 constexpr size_t kStageCopyBytes = 4096;
 
@@ -172,6 +174,7 @@ struct Ctx {
   int k1_stages = 0;        // stages of the staged pass (0: kStages)
   int k1_warps = 0;         // compute warps per block of the staged pass (0: kStageWarps)
   int k1_unit_rows = 0;     // lattice rows per unit of the staged pass (0: by copy size)
+  int k1_nodes = 0;         // nodes per compute lane of the staged pass, 16-bit (0: default)
   unsigned long long stage_wait_ns = 1000000000ull;  // limit of a staged pass's waits (ns)
   int smem_optin = 0;       // shared memory a block may opt in to (bytes)
   uint64_t config_gen = 0;  // bumped by every call that changes what a queued step launches

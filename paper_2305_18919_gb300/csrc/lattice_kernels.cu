@@ -805,14 +805,57 @@ __device__ __forceinline__ void staged_quad(const S *rows, int stride, int x0, c
     *reinterpret_cast<uint2 *>(fout + (size_t)i * P.ncell + n) = make_uint2(lo[i], hi[i]);
 }
 
-// K1s: persistent staged stream-collide (not the first step of a run). blockDim.x = 32 (NC + 1), NC <= 8:
-// warps 0 .. NC-1 compute, warp NC produces. Block b takes units b, b + gridDim.x, ...
-// NPT nodes per compute lane: 2 for FP32, 4 for 16-bit storage.
+// Compute lanes, 16-bit storage, two nodes x0, x0 + 1 (x0 even): one 4-byte word per row,
+// plus the neighbouring 2-byte value for the directions that move along x; the node pair is
+// collided exactly as each pair of the four-node form.
 template <typename S, bool FORCE>
-__global__ void __launch_bounds__(288, 1) stream_collide_staged_kernel(
+__device__ __forceinline__ void staged_pair16(const S *rows, int stride, int x0, const UnitRows &u,
+                                              const LatParams<float> &P, S *__restrict__ fout,
+                                              size_t n) {
+  using V2 = typename Storage<S>::V2;
+  const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;  // source of node x0 for c_x = +1
+  const int xp = x0 + 2 == P.nx ? 0 : x0 + 2;  // source of node x0 + 1 for c_x = -1
+  float2 g[Q];
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const S *row = rows + i * stride;
+    const unsigned int w = *reinterpret_cast<const unsigned int *>(row + x0);
+    const bool bounced = (cz(i) > 0 && u.wall_below) || (cz(i) < 0 && u.wall_above);
+    unsigned int pr;
+    if (bounced || cx(i) == 0) {
+      pr = w;
+    } else if (cx(i) > 0) {  // sources x0 - 1, x0
+      const unsigned int e = *reinterpret_cast<const unsigned short *>(row + xm);
+      pr = __byte_perm(e, w, 0x5410);
+    } else {  // sources x0 + 1, x0 + 2
+      const unsigned int e = *reinterpret_cast<const unsigned short *>(row + xp);
+      pr = __byte_perm(w, e, 0x5432);
+    }
+    g[i] = widen_pair(as_pair<V2>(pr));
+    if (bounced) {  // stored units: the wall term times k_i
+      const float wall = (cz(i) > 0 ? P.wb[i] : P.wt[i]) * float(kscale<S>(i));
+      g[i] = add2(g[i], dup(wall));
+    }
+  }
+  const float F[3] = {P.g[0], P.g[1], P.g[2]};
+  collide_pair_scaled<FORCE>(g, F, P, float(Storage<S>::K));
+#pragma unroll
+  for (int i = 0; i < Q; i++)
+    *reinterpret_cast<unsigned int *>(fout + (size_t)i * P.ncell + n) = as_bits(narrow_pair<V2>(g[i]));
+}
+
+// Launch bound of the staged kernel: 8 compute warps and the copying warp with four nodes per
+// lane (the four-node form needs ~170 registers), 16 + 1 warps with two.
+__host__ __device__ constexpr int staged_threads(int npt) { return npt == 4 ? 288 : 544; }
+
+// K1s: persistent staged stream-collide (not the first step of a run). blockDim.x = 32 (NC + 1)
+// (NC <= 8 with NPT = 4, <= 16 with NPT = 2): warps 0 .. NC-1 compute, warp NC produces. Block
+// b takes units b, b + gridDim.x, ... NPT nodes per compute lane: 2 for FP32, 2 or 4 for 16-bit
+// storage.
+template <typename S, bool FORCE, int NPT>
+__global__ void __launch_bounds__(staged_threads(NPT), 1) stream_collide_staged_kernel(
     const S *__restrict__ fin, S *__restrict__ fout, const LatParams<float> P,
     const StageGeom G, int *__restrict__ health) {
-  constexpr int NPT = sizeof(S) == 2 ? 4 : 2;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long *full = reinterpret_cast<unsigned long long *>(smem);
   unsigned long long *empty = full + G.D;
@@ -885,8 +928,10 @@ __global__ void __launch_bounds__(288, 1) stream_collide_staged_kernel(
     for (int w = warp * 32 + lane; w < G.R * per_row; w += NC * 32) {
       const int r = w / per_row, x0 = NPT * (w - r * per_row);
       const size_t n = (size_t)u.z * plane + (size_t)(u.y0 + r) * P.nx + x0;
-      if constexpr (sizeof(S) == 2)
+      if constexpr (sizeof(S) == 2 && NPT == 4)
         staged_quad<S, FORCE>(stage + (size_t)r * P.nx, G.R * P.nx, x0, u, P, fout, n);
+      else if constexpr (sizeof(S) == 2)
+        staged_pair16<S, FORCE>(stage + (size_t)r * P.nx, G.R * P.nx, x0, u, P, fout, n);
       else
         staged_pair<FORCE>(stage + (size_t)r * P.nx, G.R * P.nx, x0, u, P, fout, n);
     }
@@ -1170,13 +1215,21 @@ cudaError_t stream_collide_quad_t(Ctx &c, int first, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Nodes per compute lane of the staged pass: 2 for FP32; for 16-bit storage k1_nodes, by
+// default kStageNodes16.
+template <typename S>
+int staged_nodes(const Ctx &c) {
+  if (sizeof(S) != 2) return 2;
+  return c.k1_nodes > 0 ? c.k1_nodes : kStageNodes16;
+}
+
 // Shape of the staged pass on context c (false where it does not apply: a row of the storage
 // type that is not a whole number of 16-byte blocks, or too little shared memory for two
 // stages). R lattice rows per unit (`rows`, or by default as many as keep one population's
 // copy within kStageCopyBytes): the copies are few and large, which the copy engine needs.
 template <typename S>
 bool stage_geom(const Ctx &c, int stages, int rows, StageGeom &G, size_t &smem) {
-  constexpr int NPT = sizeof(S) == 2 ? 4 : 2;
+  const int NPT = staged_nodes<S>(c);
   const size_t row_bytes = (size_t)c.nx * sizeof(S);
   if (row_bytes % 16 != 0 || c.nx % NPT != 0) return false;
   auto fits = [&](int r, int d) { return kStageHeader + (size_t)d * r * Q * row_bytes <= (size_t)c.smem_optin; };
@@ -1201,9 +1254,10 @@ bool stage_geom(const Ctx &c, int stages, int rows, StageGeom &G, size_t &smem) 
   return true;
 }
 
-template <typename S, bool FORCE>
+template <typename S, bool FORCE, int NPT>
 cudaError_t launch_staged(Ctx &c, const StageGeom &G, size_t smem, int nc, cudaStream_t st) {
-  auto kern = stream_collide_staged_kernel<S, FORCE>;
+  auto kern = stream_collide_staged_kernel<S, FORCE, NPT>;
+  if (32 * (nc + 1) > staged_threads(NPT)) nc = staged_threads(NPT) / 32 - 1;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // one block per SM of the lattice partition, each working through its share of the units
@@ -1246,8 +1300,12 @@ cudaError_t stream_collide_staged_t(Ctx &c, cudaStream_t st, bool *used) {
       return cudaSuccess;
     *used = true;
     const bool force = c.g[0] != 0.0 || c.g[1] != 0.0 || c.g[2] != 0.0;
-    return force ? launch_staged<S, true>(c, G, smem, nc, st)
-                 : launch_staged<S, false>(c, G, smem, nc, st);
+    if constexpr (sizeof(S) == 2)
+      if (staged_nodes<S>(c) == 4)
+        return force ? launch_staged<S, true, 4>(c, G, smem, nc, st)
+                     : launch_staged<S, false, 4>(c, G, smem, nc, st);
+    return force ? launch_staged<S, true, 2>(c, G, smem, nc, st)
+                 : launch_staged<S, false, 2>(c, G, smem, nc, st);
   }
 }
 

@@ -46,14 +46,16 @@ def test_staged_equals_direct(precision, shape, force):
     staged.close()
 
 
-@pytest.mark.parametrize("stages,warps,rows", [(2, 1, 0), (3, 5, 1), (8, 8, 4), (2, 8, 2),
-                                               (5, 2, 0), (4, 3, 4)])
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_stage_depths_and_warps(precision, stages, warps, rows):
-    """Buffer depths, warp counts and unit heights, including units of one row and units
-    whose rows wrap around y (rows of 4 over ny = 20)."""
+@pytest.mark.parametrize("stages,warps,rows,nodes", [(2, 1, 0, 0), (3, 5, 1, 0), (8, 8, 4, 4),
+                                                     (2, 8, 2, 2), (5, 2, 0, 2), (4, 3, 4, 4),
+                                                     (2, 16, 0, 2), (3, 12, 4, 2), (4, 16, 1, 4)])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_stage_depths_and_warps(precision, stages, warps, rows, nodes):
+    """Buffer depths, warp counts, unit heights and nodes per lane, including units of one row,
+    units whose rows wrap around y (rows of 4 over ny = 20) and more warps than the four-node
+    form takes (it keeps 8)."""
     direct, staged = _pair((48, 20, 11, False), precision, True, seed=5)
-    staged.set_stream_collide("staged", stages, warps, rows)
+    staged.set_stream_collide("staged", stages, warps, rows, nodes)
     direct.step(9)
     staged.step(9)
     np.testing.assert_array_equal(staged.populations(), direct.populations())
@@ -96,12 +98,13 @@ def test_staged_full_size_against_direct():
 def test_set_stream_collide_arguments():
     from paper_2305_18919_gb300 import binding
     lat = binding.Lattice(8, 8, 6, 0.8)
-    for args in ((3, 0, 0, 0), (-1, 0, 0, 0), (1, 1, 0, 0), (1, 9, 0, 0), (1, 0, -1, 0), (1, 0, 9, 0),
-                 (1, 0, 0, 3), (1, 0, 0, 16), (1, 0, 0, -2)):
+    for args in ((3, 0, 0, 0, 0), (-1, 0, 0, 0, 0), (1, 1, 0, 0, 0), (1, 9, 0, 0, 0),
+                 (1, 0, -1, 0, 0), (1, 0, 17, 0, 0), (1, 0, 0, 3, 0), (1, 0, 0, 16, 0),
+                 (1, 0, 0, -2, 0), (1, 0, 0, 0, 3), (1, 0, 0, 0, 1)):
         with pytest.raises(binding.IBLBError) as e:
             lat._check(lat._L.iblb_set_stream_collide(lat.h, *args))
         assert e.value.code == binding.IBLB_EINVAL
-    lat.set_stream_collide("direct", 2, 8, 8)
+    lat.set_stream_collide("direct", 2, 8, 8, 2)
     lat.set_stream_collide("staged")
     lat.step(3)
     lat.close()
