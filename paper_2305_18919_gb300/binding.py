@@ -367,8 +367,9 @@ class Lattice:
 
 
 class Batch:
-    """Independent contexts advanced together (iblb_batch_*): one CUDA graph launch per two
-    steps for the whole ensemble. `contexts` are Lattice views of the batch's contexts."""
+    """Independent contexts advanced together (iblb_batch_*): each kernel of a step is one
+    launch over all contexts of a precision. `contexts` are Lattice views of the batch's
+    contexts."""
 
     def __init__(self, descs, stream=None):
         self._L = lib()

@@ -353,7 +353,7 @@ int iblb_batch_tune(iblb_batch *b, int32_t trials) {
       it = best_rows.emplace(key, pick).first;
     }
     c.k1_rows = it->second;
-    c.config_gen++;  // the launch shape changed: a captured graph is stale
+    c.config_gen++;  // the launch shape changed: the batched records are stale
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -378,8 +378,8 @@ int iblb_batch_step(iblb_batch *b, int32_t nsteps) {
     BATCH_TRY(b, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
   }
   int done = 0;
-  // a freshly initialised state is collided in place by its first step, which the graph
-  // does not hold: every instance takes that step directly
+  // a freshly initialised state is collided in place by its first step, which the batched
+  // kernels do not do: every instance takes that step through the single-context kernels
   bool any_fresh = false;
   for (size_t i = 0; i < n; i++) any_fresh = any_fresh || b->inst[i]->c.fresh;
   if (any_fresh) {

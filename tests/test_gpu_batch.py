@@ -1,7 +1,7 @@
 """The batched ensemble (iblb_batch_*): independent contexts of different sizes and
-precisions advanced together through one CUDA graph. Every instance must end bit for bit where
-the same context stepped alone (without an SM partition) ends, whatever the step count (fresh
-first step, graph replays, odd tail), the tuned launch shape or a reconfiguration between
+precisions advanced together, each kernel of a step one launch over all instances. Every
+instance must end bit for bit where the same context stepped alone ends, whatever the step
+count (fresh first step, pairs of batched steps, odd tail), the tuned launch shape or a reconfiguration between
 calls; a failing instance is reported by index."""
 import numpy as np
 import pytest
@@ -59,7 +59,7 @@ def test_batch_mixed_precisions_and_repeated_calls():
         v, f = wl.mesh()
         lat.add_mesh(v, f)
         lat.set_interface(wl.alpha, wl.kV, wl.eps, wl.xi, wl.wall_force_on, wl.volume_force_on)
-    for k in (5, 4, 3):  # graph replays across calls, tails of one step
+    for k in (5, 4, 3):  # batched pairs across calls, tails of one step
         b.step(k)
     for lat, wl, p in zip(b.contexts, wls, precs):
         _same(lat, _alone(wl, p, [12]))
