@@ -232,8 +232,9 @@ def replica_mlups(world: int, cells: int, steps: int, seconds: float) -> float:
 def k1_kernel_name(lat, precision):
     """Name of the kernel that runs the full-lattice pass of the timed steps."""
     storage = {"fp64": "double", "fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}
-    if lat.stream_collide_staged():
-        return f"stream_collide_staged_kernel<{storage[precision]},false>"
+    if lat.stream_collide_staged():  # four nodes per compute lane with 16-bit storage
+        nodes = 4 if precision in ("fp16", "bf16") else 2
+        return f"stream_collide_staged_kernel<{storage[precision]},false,{nodes}>"
     if precision in ("fp16", "bf16"):
         return f"stream_collide_quad_kernel<{storage[precision]},false,false>"
     real = "double" if precision == "fp64" else "float"
