@@ -341,7 +341,7 @@ def time_adjoint(steps, every, ref_steps=2):
     out = {"workload": wl.name, "steps": steps, "checkpoint_every": every,
            "value": round(steps / t_adj, 1), "unit": "adjoint steps/s",
            "forward_steps_per_s": round(steps / t_fwd, 1),
-           "observable": "wetted radius", "J": round(float(radius), 4),
+           "observable": "wetted radius", "J": round(float(radius.detach()), 4),
            "dJ_dtheta": [float(x) for x in g],
            "path": "iblb_adjoint_record + iblb_adjoint_gradient (recompute per segment + reverse step), FP64"}
     try:

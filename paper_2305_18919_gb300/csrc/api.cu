@@ -555,9 +555,16 @@ int enqueue_steps(Ctx &c, int nsteps) {
     c.cur ^= 1;
     c.fresh = 0;
     if (c.nv) {
-      CUDA_TRY(c, cudaStreamWaitEvent(c.ib, c.ev_coll, 0));
-      CUDA_TRY(c, iblb::launch_shell_velocity(c, c.ib));
-      CUDA_TRY(c, iblb::launch_interpolate_advect(c, c.ib));
+      // the shell velocity and the interpolation of the call's last step have no next lattice
+      // pass to hide under: with partitions they run on the caller's stream, on all SMs
+      cudaStream_t tail = c.ib;
+      if (s == nsteps - 1 && c.green[0]) {
+        tail = c.stream;
+        CUDA_TRY(c, cudaStreamWaitEvent(c.stream, c.ev_force, 0));
+      }
+      CUDA_TRY(c, cudaStreamWaitEvent(tail, c.ev_coll, 0));
+      CUDA_TRY(c, iblb::launch_shell_velocity(c, tail));
+      CUDA_TRY(c, iblb::launch_interpolate_advect(c, tail));
       c.kernel_launches += 2;
       c.map ^= 1;
       c.have_force = 1;
