@@ -144,3 +144,34 @@ def test_autograd_function_contact_angle_and_wetted_radius():
     _masked_fd(wl, N, lambda qq, s: ad.contact_angle(qq, faces, z_wall=z_ref, select=s),
                g_angle.numpy(), sel_v)
     _masked_fd(wl, N, lambda qq, s: ad.wetted_radius(qq, faces, select=s), g_r.numpy(), sel_f)
+
+
+def test_adjoint_24_cubed_200_steps_vs_fp64_reference():
+    """The check the 64^3 adjoint workload names: a 24^3, subdivision-2 copy of it (the same
+    particle class, alpha and wall strength, R scaled by 24/64) over 200 steps, the GPU adjoint
+    against the FP64 CPU reference gradient."""
+    from oracle import adjoint as oa
+    base = inputs.adjoint_wetting_64()
+    wl = inputs.scaled_wetting(24, 24, 2, base.radius * 24 / 64, alpha=base.alpha, eps=base.eps,
+                               precision="fp64")
+    _, g_ref, q_ref = oa.gradient(wl, 200, objective)
+    g, q, _ = _gpu_gradient(wl, 200, 100)
+    assert np.abs(q - q_ref).max() < 1e-10
+    np.testing.assert_allclose(g, g_ref, rtol=1e-6, atol=1e-11 * np.abs(g_ref).max())
+
+
+def test_full_size_adjoint_vs_finite_differences():
+    """The 64^3 adjoint workload itself (subdivision 4, 5000 steps, a state copy every 100):
+    the gradient of the wetted radius through torch.autograd against central differences of
+    full GPU runs, with the face selection held at the base run's."""
+    from paper_2305_18919_gb300 import adjoint as ad
+    wl = inputs.adjoint_wetting_64()
+    _, faces = wl.mesh()
+    N = 5000
+    theta = torch.tensor(list(wl.alpha) + [wl.eps], dtype=torch.float64, requires_grad=True)
+    q = ad.run(theta, wl, N, every=100)
+    gz = (q[faces[:, 0], 2] + q[faces[:, 1], 2] + q[faces[:, 2], 2]).detach() / 3
+    sel_f = torch.as_tensor(gz - 0.5 < 1.0)
+    r = ad.wetted_radius(q, faces, select=sel_f)
+    (g_r,) = torch.autograd.grad(r, theta)
+    _masked_fd(wl, N, lambda qq, s: ad.wetted_radius(qq, faces, select=s), g_r.numpy(), sel_f)

@@ -154,3 +154,19 @@ def test_more_instances_than_one_launch_holds():
         assert np.array_equal(b.contexts[k].populations(), ref.populations())
         ref.close()
     b.close()
+
+
+def test_full_ensemble_sampled_instances():
+    """The 96-box ensemble of the benchmark (33 M nodes, edges from {48, 64, 80, 96}) in the
+    launch configuration the benchmark times: after 5 steps, sampled instances equal the same
+    contexts stepped alone, bit for bit."""
+    from paper_2305_18919_gb300 import binding
+    wls = inputs.wetting_ensemble(96, 2305)
+    b = binding.Batch.from_workloads(wls)
+    b.tune(trials=1)
+    b.step(5)
+    assert all(s == 0 for s in b.status())
+    for k in (0, 31, 58, 95):
+        ref = _alone(wls[k], "fp32", [5])
+        _same(b.contexts[k], ref)
+    b.close()

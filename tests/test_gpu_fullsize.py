@@ -97,3 +97,20 @@ def test_beyond_32_bit_element_offsets(precision, kind):
                    (slice(n - p, n), slice(0, p))):
         assert np.array_equal(r_b[:, ys, xs], r_s)
         assert np.array_equal(u_b[:, ys, xs], u_s)
+
+
+def test_wetting_128_full_size():
+    """The static-wetting workload at its full size (128 x 128 x 96, R = 20, subdivision 5,
+    FP32, the first of its eight wall strengths): three coupled steps against the oracle."""
+    wl = inputs.wetting_128x128x96()
+    ref, gpu = make_pair(wl, "fp32")
+    ref.step(3)
+    gpu.step(3)
+    assert np.abs(gpu.vertices() - ref.vertices()).max() <= 1e-6 * wl.radius
+    _, u0 = ref.fields()
+    _, u1 = gpu.fields()
+    assert rel_l2(u1[1:-1], u0[1:-1]) < 1e-5
+    phi0, _ = ref.forces()
+    assert rel_l2(gpu.forces(), phi0) < 2e-6
+    ref.close()
+    gpu.close()
