@@ -317,16 +317,17 @@ def time_ensemble(steps, warmup, n=96, seed=2305, ib_sms=0):
 
 
 def time_adjoint(steps, every, ref_steps=2):
-    """Adjoint steps/s on the 64^3 wetting workload (FP64): iblb_adjoint_record of `steps`
-    steps with a state copy every `every`, then iblb_adjoint_gradient of the wetted radius
-    (torch observable); the autograd reference (oracle/adjoint.py, one host thread) is timed on
-    `ref_steps` steps of the same workload."""
+    """Adjoint steps/s on the 64^3 wetting workload with an FP32 forward run: iblb_adjoint_record
+    of `steps` steps with a state copy every `every`, then iblb_adjoint_gradient (reverse pass
+    in double) of the wetted radius (torch observable); the autograd reference
+    (oracle/adjoint.py, one host thread, FP64) is timed on `ref_steps` steps of the same
+    workload."""
     import torch
     from paper_2305_18919_gb300 import adjoint as ad
     from paper_2305_18919_gb300 import binding
     wl = inputs.adjoint_wetting_64()
     _, faces = wl.mesh()
-    lat = binding.Lattice.from_workload(wl, precision="fp64")
+    lat = binding.Lattice.from_workload(wl, precision="fp32")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     lat.adjoint_record(steps, every)
@@ -343,7 +344,8 @@ def time_adjoint(steps, every, ref_steps=2):
            "forward_steps_per_s": round(steps / t_fwd, 1),
            "observable": "wetted radius", "J": round(float(radius.detach()), 4),
            "dJ_dtheta": [float(x) for x in g],
-           "path": "iblb_adjoint_record + iblb_adjoint_gradient (recompute per segment + reverse step), FP64"}
+           "path": "iblb_adjoint_record + iblb_adjoint_gradient (recompute per segment + reverse "
+                   "step): FP32 forward, reverse in double"}
     try:
         torch.set_num_threads(1)
         from oracle import adjoint as oa

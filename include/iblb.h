@@ -225,7 +225,10 @@ int iblb_batch_status(const iblb_batch *batch, int32_t *status);
 
 /* ---- Adjoint: gradients of an observable of the final vertex positions ----------------------
    The discrete adjoint of the coupled step (Sec. III) with respect to the interface parameters
-   theta = (alpha1, alpha2, alpha3, eps) of Eq. 2 and Eq. 19; IBLB_FP64 contexts with a mesh.
+   theta = (alpha1, alpha2, alpha3, eps) of Eq. 2 and Eq. 19; IBLB_FP64 or IBLB_FP32 contexts
+   with a mesh. The forward run is the context's own; the reverse pass is in double, and with
+   FP32 storage it linearises the double-precision step about the recomputed FP32 trajectory
+   (the copies keep the populations as stored, so the recomputation repeats it bit for bit).
 
    iblb_adjoint_record advances nsteps steps from the current state (as iblb_step would) and keeps
    a copy of the state (populations and positions) every `every` steps on the device: memory
@@ -238,7 +241,7 @@ int iblb_batch_status(const iblb_batch *batch, int32_t *status);
    the recording stays valid for further calls with other dJdq.
 
    iblb_adjoint_release frees the recording and the work arrays (iblb_destroy also does).
-   Errors: IBLB_EINVAL (not FP64, no mesh, nothing recorded, nsteps or every < 1), the health
+   Errors: IBLB_EINVAL (16-bit storage, no mesh, nothing recorded, nsteps or every < 1), the health
    errors of iblb_step during the record or the recomputation, IBLB_ENOMEM, IBLB_ECUDA. */
 int iblb_adjoint_record(iblb_ctx *ctx, int32_t nsteps, int32_t every);
 int iblb_adjoint_gradient(iblb_ctx *ctx, const double *dJdq, double *dJdtheta);

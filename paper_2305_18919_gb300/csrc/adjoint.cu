@@ -1,6 +1,8 @@
 // Discrete adjoint of the coupled IB-LB step (Sec. III), in double precision: gradients of an
 // observable of the final vertex positions with respect to the interface parameters
-// theta = (alpha1, alpha2, alpha3, eps) of Eqs. 2 and 19.
+// theta = (alpha1, alpha2, alpha3, eps) of Eqs. 2 and 19. The forward run is that of the
+// context, FP64 or FP32; with FP32 the reverse pass linearises the double-precision step about
+// the recomputed FP32 trajectory.
 //
 // One forward step n maps (P_n, q_n) to (P_{n+1}, q_{n+1}), P being the post-collision
 // populations the pull scheme keeps between steps:
@@ -526,9 +528,17 @@ __global__ void adj_accumulate_kernel(const double *__restrict__ sums, double *_
 
 // --- host side ---------------------------------------------------------------------------
 
+// FP32 populations widened to double.
+__global__ void widen_kernel(const float *__restrict__ in, double *__restrict__ out, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    out[k] = (double)in[k];
+}
+
 struct Adjoint {
   int nsteps = 0, every = 0, first_fresh = 0;
-  std::vector<double *> ck_P, ck_q;   // state at steps 0, K, 2K, ..., nsteps
+  std::vector<void *> ck_P;           // populations at steps 0, K, 2K, ..., nsteps (storage type)
+  std::vector<double *> ck_q;         // positions at the same steps
   std::vector<double *> seg_P, seg_q; // states of the segment being reversed
   double *lam_P[2] = {nullptr, nullptr};
   double *lam_q = nullptr, *lam_qn = nullptr, *lam_phi = nullptr, *lam_F = nullptr,
@@ -541,7 +551,8 @@ void free_all(Adjoint *a) {
   auto f = [](double *p) {
     if (p) cudaFree(p);
   };
-  for (double *p : a->ck_P) f(p);
+  for (void *p : a->ck_P)
+    if (p) cudaFree(p);
   for (double *p : a->ck_q) f(p);
   for (double *p : a->seg_P) f(p);
   for (double *p : a->seg_q) f(p);
@@ -607,9 +618,26 @@ LatArgs lat_args(const Ctx &c) {
   return L;
 }
 
-int snapshot(Ctx &c, double *P, double *q) {
-  ADJ_TRY(c, cudaMemcpyAsync(P, c.f[c.cur], (size_t)Q * c.ncell * sizeof(double),
+// A checkpoint: the populations as stored (so that restoring them continues bit for bit) and
+// the positions.
+int snapshot_raw(Ctx &c, void *P, double *q) {
+  ADJ_TRY(c, cudaMemcpyAsync(P, c.f[c.cur], (size_t)Q * c.ncell * c.pop_size,
                              cudaMemcpyDeviceToDevice, c.stream));
+  ADJ_TRY(c, cudaMemcpyAsync(q, c.q, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c.stream));
+  return 0;
+}
+
+// A state of the segment being reversed, in double whatever the storage: the reverse step
+// linearises the double-precision step about it (for FP32 storage, about the FP32 trajectory).
+int snapshot(Ctx &c, double *P, double *q) {
+  const size_t n = (size_t)Q * c.ncell;
+  if (c.pop_size == sizeof(double)) {
+    ADJ_TRY(c, cudaMemcpyAsync(P, c.f[c.cur], n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  } else {
+    widen_kernel<<<c.sm_count * 8, 256, 0, c.stream>>>((const float *)c.f[c.cur], P, n);
+    ADJ_TRY(c, cudaGetLastError());
+  }
   ADJ_TRY(c, cudaMemcpyAsync(q, c.q, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToDevice,
                              c.stream));
   return 0;
@@ -678,7 +706,8 @@ extern "C" {
 int iblb_adjoint_record(iblb_ctx *h, int32_t nsteps, int32_t every) {
   if (!h) return IBLB_EINVAL;
   Ctx &c = h->c;
-  if (c.precision != IBLB_FP64) return iblb::afail(c, IBLB_EINVAL, "the adjoint needs an IBLB_FP64 context");
+  if (c.precision != IBLB_FP64 && c.precision != IBLB_FP32)
+    return iblb::afail(c, IBLB_EINVAL, "the adjoint needs an IBLB_FP64 or IBLB_FP32 context");
   if (c.nv == 0) return iblb::afail(c, IBLB_EINVAL, "no mesh has been added");
   if (nsteps < 1 || every < 1) return iblb::afail(c, IBLB_EINVAL, "nsteps and every must be >= 1");
   iblb::adjoint_free(c);
@@ -690,20 +719,21 @@ int iblb_adjoint_record(iblb_ctx *h, int32_t nsteps, int32_t every) {
   const size_t pn = (size_t)iblb::Q * c.ncell, qn = (size_t)3 * c.nv;
   const int nck = (nsteps + a->every - 1) / a->every + 1;
   for (int k = 0; k < nck; k++) {
-    double *P = nullptr, *q = nullptr;
-    ADJ_TRY(c, iblb::dmalloc(&P, pn));
+    void *P = nullptr;
+    double *q = nullptr;
+    ADJ_TRY(c, cudaMalloc(&P, pn * c.pop_size));
     a->ck_P.push_back(P);
     ADJ_TRY(c, iblb::dmalloc(&q, qn));
     a->ck_q.push_back(q);
   }
   ADJ_TRY(c, cudaStreamSynchronize(c.stream));
-  if (int rc = iblb::snapshot(c, a->ck_P[0], a->ck_q[0])) return rc;
+  if (int rc = iblb::snapshot_raw(c, a->ck_P[0], a->ck_q[0])) return rc;
   int done = 0;
   for (int k = 1; k < nck; k++) {
     const int n = nsteps - done < a->every ? nsteps - done : a->every;
     if (int rc = iblb::run_steps(c, n)) return rc;
     done += n;
-    if (int rc = iblb::snapshot(c, a->ck_P[k], a->ck_q[k])) return rc;
+    if (int rc = iblb::snapshot_raw(c, a->ck_P[k], a->ck_q[k])) return rc;
   }
   ADJ_TRY(c, cudaStreamSynchronize(c.stream));
   return IBLB_OK;

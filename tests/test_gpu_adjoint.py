@@ -1,4 +1,4 @@
-"""The discrete adjoint on the GPU (iblb_adjoint_*, FP64) against the reference gradients of
+"""The discrete adjoint on the GPU (iblb_adjoint_*, FP64 and FP32 forward runs) against the reference gradients of
 oracle/adjoint.py (the oracle's step restated in float64 PyTorch and differentiated by
 autograd, itself pinned to finite differences of the C oracle), and against central finite
 differences of the GPU's own forward runs on a larger box."""
@@ -83,11 +83,12 @@ def test_gpu_adjoint_equals_finite_differences_of_gpu_runs():
 def test_adjoint_rejects_what_it_cannot_do():
     from paper_2305_18919_gb300 import binding
     wl = _small()
-    lat = binding.Lattice.from_workload(wl, precision="fp32")
-    with pytest.raises(binding.IBLBError) as e:
-        lat.adjoint_record(5, 5)
-    assert e.value.code == binding.IBLB_EINVAL
-    lat.close()
+    for precision in ("fp16", "bf16"):  # 16-bit storage has no adjoint
+        lat = binding.Lattice.from_workload(wl, precision=precision)
+        with pytest.raises(binding.IBLBError) as e:
+            lat.adjoint_record(5, 5)
+        assert e.value.code == binding.IBLB_EINVAL
+        lat.close()
     lat = binding.Lattice.from_workload(wl, precision="fp64")
     with pytest.raises(binding.IBLBError):
         lat.adjoint_gradient(np.zeros((lat.nv, 3)))  # nothing recorded
@@ -175,3 +176,36 @@ def test_full_size_adjoint_vs_finite_differences():
     r = ad.wetted_radius(q, faces, select=sel_f)
     (g_r,) = torch.autograd.grad(r, theta)
     _masked_fd(wl, N, lambda qq, s: ad.wetted_radius(qq, faces, select=s), g_r.numpy(), sel_f)
+
+
+def _gradient_with(wl, nsteps, every, precision):
+    from paper_2305_18919_gb300 import binding
+    lat = binding.Lattice.from_workload(wl, precision=precision)
+    lat.adjoint_record(nsteps, every)
+    q = lat.vertices()
+    g = lat.adjoint_gradient(objective_grad(q))
+    lat.close()
+    return g, q
+
+
+@pytest.mark.parametrize("every", [30, 7])
+def test_fp32_forward_adjoint(every):
+    """With FP32 storage the forward run (and its recomputation) is FP32 and the reverse pass
+    linearises the double step about that trajectory: the gradient is the FP64 one to within
+    what the FP32 trajectory's rounding moves it, and a second call recomputes the same
+    trajectory (the reverse pass's dense spreading sums with atomics, so the two gradients agree
+    to rounding, not bit for bit)."""
+    from paper_2305_18919_gb300 import binding
+    wl = inputs.scaled_wetting(32, 24, 3, 6.0, alpha=(4e-3, 2e-3, 1e-3), eps=5e-4,
+                               precision="fp64")
+    g64, q64 = _gradient_with(wl, 120, every, "fp64")
+    lat = binding.Lattice.from_workload(wl, precision="fp32")
+    lat.adjoint_record(120, every)
+    q32 = lat.vertices()
+    g32 = lat.adjoint_gradient(objective_grad(q32))
+    g32b = lat.adjoint_gradient(objective_grad(q32))
+    lat.close()
+    np.testing.assert_allclose(g32b, g32, rtol=1e-12)
+    assert np.abs(q32 - q64).max() < 1e-5 * wl.radius
+    # measured on GB300: 2e-8 .. 2.5e-6 relative over these 120 steps
+    np.testing.assert_allclose(g32, g64, rtol=2e-5)
