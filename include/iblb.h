@@ -43,6 +43,8 @@ extern "C" {
 #define IBLB_EUNSTABLE (-4) /* health check failed: NaN, |qdot| >= 0.1, vertex within 0.05 of a
                                wall plane, or |V/V0 - 1| > 0.05 */
 #define IBLB_ECAPACITY (-5) /* an internal bound was exceeded (active-tile table) */
+#define IBLB_ETIMEOUT (-6)  /* a bounded wait inside a kernel gave up (the staged stream-collide
+                               pass, iblb_set_stage_wait_limit); the context stays usable */
 
 #define IBLB_FP64 1 /* populations and interface arithmetic in double */
 #define IBLB_FP32 2 /* populations (stored as f_i - w_i rho0) and interface forces in float;
@@ -112,13 +114,19 @@ int iblb_init_equilibrium(iblb_ctx *ctx, const double *rho, const double *u);
 
 /* Advance nsteps coupled steps (order above). Work is queued on the stream; the call
    synchronises once at its end to read the health word and returns IBLB_EUNSTABLE or
-   IBLB_ECAPACITY if a check failed during any of the steps. */
+   IBLB_ECAPACITY if a check failed during any of the steps, IBLB_ETIMEOUT if a bounded wait
+   of the staged stream-collide pass gave up. */
 int iblb_step(iblb_ctx *ctx, int32_t nsteps);
 
 /* rho [nz][ny][nx] and u [nz][ny][nx][3] of the current post-streaming state; u carries half
    of the force of the last spreading step (none before the first step) plus the body force.
    Wall-layer nodes report rho0 and their wall velocity. */
 int iblb_read_fields(iblb_ctx *ctx, double *rho, double *u);
+
+/* Same as iblb_read_fields into device buffers rho_dev [nz][ny][nx] and u_dev [nz][ny][nx][3]
+   (doubles, caller-owned, e.g. torch tensors), ordered on the context's stream; does not
+   synchronise. */
+int iblb_read_fields_device(iblb_ctx *ctx, double *rho_dev, double *u_dev);
 
 /* Populations [19][nz][ny][nx] of the current post-streaming state (wall layers: 0). */
 int iblb_read_populations(iblb_ctx *ctx, double *f);
@@ -264,9 +272,8 @@ int iblb_adjoint_release(iblb_ctx *ctx);
    fits in shared memory; warps: 0 (8) or 1..16 (at most 8 with four nodes per lane); rows: 0
    (as many as keep one copy within 4 KB) or a power of two up to 16 that divides ny; nodes:
    nodes per compute lane with 16-bit storage, 0 (the default), 2 or 4 (FP32 always takes 2).
-   IBLB_EINVAL for anything else. A staged block
-   whose wait for its copies gives up (after 1 s) returns early, and iblb_step then returns
-   IBLB_ECUDA. */
+   IBLB_EINVAL for anything else. A staged block whose wait for its copies gives up (after
+   1 s) returns early, and iblb_step then returns IBLB_ETIMEOUT. */
 #define IBLB_STREAM_COLLIDE_AUTO 0
 #define IBLB_STREAM_COLLIDE_STAGED 1
 #define IBLB_STREAM_COLLIDE_DIRECT 2
@@ -277,8 +284,8 @@ int iblb_set_stream_collide(iblb_ctx *ctx, int32_t kind, int32_t stages, int32_t
    test, so that a block's first wait, which comes before its copies complete, gives up; this
    exercises the timeout path). A wait that runs out records the timeout in the health word
    and its block stops; before the block exits, its copying warp still waits up to 1 s for the
-   copies it has in flight. iblb_step then returns IBLB_ECUDA and the populations of that step
-   are incomplete; the context stays usable (iblb_init_equilibrium or iblb_load_state restore
+   copies it has in flight. iblb_step then returns IBLB_ETIMEOUT and the populations of that
+   step are incomplete; the context stays usable (iblb_init_equilibrium or iblb_load_state restore
    a state). IBLB_EINVAL outside the range. */
 int iblb_set_stage_wait_limit(iblb_ctx *ctx, int64_t ns);
 

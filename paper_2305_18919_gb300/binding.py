@@ -19,6 +19,7 @@ IBLB_ENOMEM = -2
 IBLB_ECUDA = -3
 IBLB_EUNSTABLE = -4
 IBLB_ECAPACITY = -5
+IBLB_ETIMEOUT = -6
 IBLB_FP64 = 1
 IBLB_FP32 = 2
 IBLB_FP16 = 3
@@ -70,6 +71,7 @@ SIGNATURES = {
     "iblb_init_equilibrium": (_i32, [_vp, _dp, _dp]),
     "iblb_step": (_i32, [_vp, _i32]),
     "iblb_read_fields": (_i32, [_vp, _dp, _dp]),
+    "iblb_read_fields_device": (_i32, [_vp, _vp, _vp]),
     "iblb_read_populations": (_i32, [_vp, _dp]),
     "iblb_read_vertices": (_i32, [_vp, _i32, _dp]),
     "iblb_read_vertices_device": (_i32, [_vp, _i32, _vp]),
@@ -271,6 +273,17 @@ class Lattice:
         rho = np.empty((nz, ny, nx))
         u = np.empty((nz, ny, nx, 3))
         self._check(self._L.iblb_read_fields(self.h, _dptr(rho), _dptr(u)))
+        return rho, u
+
+    def fields_device(self):
+        """rho [nz][ny][nx] and u [nz][ny][nx][3] as float64 torch tensors on the context's
+        device, written by the library on the context's stream (iblb_read_fields_device)."""
+        import torch
+        nx, ny, nz = self.shape
+        rho = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
+        u = torch.empty((nz, ny, nx, 3), dtype=torch.float64, device="cuda")
+        self._check(self._L.iblb_read_fields_device(self.h, ctypes.c_void_p(rho.data_ptr()),
+                                                    ctypes.c_void_p(u.data_ptr())))
         return rho, u
 
     def populations(self):

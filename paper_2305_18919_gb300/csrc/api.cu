@@ -83,7 +83,7 @@ int read_health(Ctx &c, int *h) {
 // An unstable run reports that first: its garbage positions can also leave tiles unmarked.
 int health_error(Ctx &c, int h) {
   if (h & iblb::H_TIMEOUT)
-    return fail(c, IBLB_ECUDA, "stream-collide pipeline: a bounded wait for staged data gave up");
+    return fail(c, IBLB_ETIMEOUT, "stream-collide pipeline: a bounded wait for staged data gave up");
   const int unstable = iblb::H_NAN | iblb::H_FAST | iblb::H_WALL | iblb::H_VOLUME;
   if (!(h & unstable))
     return fail(c, IBLB_ECAPACITY, "active-tile table capacity exceeded");
@@ -604,6 +604,13 @@ int iblb_read_fields(iblb_ctx *h, double *rho, double *u) {
   CUDA_TRY(c, cudaMemcpyAsync(rho, c.dscratch, c.ncell * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CUDA_TRY(c, cudaMemcpyAsync(u, c.dscratch + c.ncell, 3 * c.ncell * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
+  return IBLB_OK;
+}
+
+int iblb_read_fields_device(iblb_ctx *h, double *rho_dev, double *u_dev) {
+  if (!h || !rho_dev || !u_dev) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  CUDA_TRY(c, iblb::launch_fields(c, rho_dev, u_dev));
   return IBLB_OK;
 }
 

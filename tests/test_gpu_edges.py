@@ -87,3 +87,20 @@ def test_rest_stays_exactly_at_rest(precision):
     fl = f[:, 1:-1]
     assert np.array_equal(fl, np.broadcast_to(w[:, None, None, None], fl.shape))
     lat.close()
+
+
+def test_fields_into_device_buffers():
+    """iblb_read_fields_device writes the same rho and u as iblb_read_fields, into torch tensors
+    on the device, ordered on the context's stream."""
+    torch = pytest.importorskip("torch")
+    from paper_2305_18919_gb300 import binding
+    wl = inputs.scaled_shear(24, 2, 5.0, alpha=(0.01, 0.01, 0.01))
+    lat = binding.Lattice.from_workload(wl, precision="fp32")
+    lat.step(7)
+    rho, u = lat.fields()
+    rho_d, u_d = lat.fields_device()
+    torch.cuda.synchronize()
+    assert rho_d.is_cuda and u_d.shape == u.shape
+    assert np.array_equal(rho_d.cpu().numpy(), rho)
+    assert np.array_equal(u_d.cpu().numpy(), u)
+    lat.close()

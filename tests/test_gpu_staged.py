@@ -146,7 +146,7 @@ def test_wait_limit_runs_out_and_context_recovers(precision):
     lat.set_stage_wait_limit(0)
     with pytest.raises(binding.IBLBError) as e:
         lat.step(2)
-    assert e.value.code == binding.IBLB_ECUDA
+    assert e.value.code == binding.IBLB_ETIMEOUT
     assert "bounded wait" in str(e.value)
     with pytest.raises(binding.IBLBError):
         lat.set_stage_wait_limit(-1)
