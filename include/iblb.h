@@ -113,10 +113,15 @@ int iblb_set_vertices(iblb_ctx *ctx, int32_t mesh_id, const double *q);
 int iblb_init_equilibrium(iblb_ctx *ctx, const double *rho, const double *u);
 
 /* Advance nsteps coupled steps (order above). Work is queued on the stream; the call
-   synchronises once at its end to read the health word and returns IBLB_EUNSTABLE or
-   IBLB_ECAPACITY if a check failed during any of the steps, IBLB_ETIMEOUT if a bounded wait
-   of the staged stream-collide pass gave up. */
+   synchronises to read the health word every `every` steps of iblb_set_health_interval (1000
+   by default) and at its end, and returns IBLB_EUNSTABLE or IBLB_ECAPACITY if a check failed
+   during the steps read so far (the steps done then stop at the end of that interval),
+   IBLB_ETIMEOUT if a bounded wait of the staged stream-collide pass gave up. */
 int iblb_step(iblb_ctx *ctx, int32_t nsteps);
+
+/* Steps between health-word reads in iblb_step: every >= 1, or 0 for one read at the end of
+   each call. IBLB_EINVAL for every < 0. */
+int iblb_set_health_interval(iblb_ctx *ctx, int32_t every);
 
 /* rho [nz][ny][nx] and u [nz][ny][nx][3] of the current post-streaming state; u carries half
    of the force of the last spreading step (none before the first step) plus the body force.

@@ -89,6 +89,7 @@ SIGNATURES = {
     "iblb_set_stream_collide": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),
     "iblb_stream_collide_staged": (_i32, [_vp]),
     "iblb_set_stage_wait_limit": (_i32, [_vp, _i64]),
+    "iblb_set_health_interval": (_i32, [_vp, _i32]),
     "iblb_mesh_volume_noalloc": (_i32, [_vp, _vp, _i32, _dp, _vp, _vp]),
     "iblb_batch_create": (_i32, [ctypes.POINTER(iblb_lattice_desc), _i32, _vp, ctypes.POINTER(_vp)]),
     "iblb_batch_destroy": (None, [_vp]),
@@ -341,6 +342,10 @@ class Lattice:
 
     def interface_sms(self) -> int:
         return int(self._L.iblb_interface_sms(self.h))
+
+    def set_health_interval(self, every):
+        """Steps between health-word reads in step() (0: once per call)."""
+        self._check(self._L.iblb_set_health_interval(self.h, int(every)))
 
     def set_stage_wait_limit(self, ns):
         """Limit (ns) of each wait of the staged stream-collide kernel (iblb_set_stage_wait_limit)."""

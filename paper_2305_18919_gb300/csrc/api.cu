@@ -508,10 +508,24 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
   if (nsteps < 0) return fail(c, IBLB_EINVAL, "nsteps < 0");
   if (nsteps == 0) return IBLB_OK;
   CUDA_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
-  if (int rc = iblb::enqueue_steps(c, nsteps)) return rc;
-  int hw = 0;
-  if (int rc = read_health(c, &hw)) return rc;
-  if (hw) return health_error(c, hw);
+  // the health word is read every health_every steps (and at the end), so that a run that goes
+  // unstable stops near where it did
+  for (int done = 0; done < nsteps;) {
+    const int n = c.health_every > 0 && c.health_every < nsteps - done ? c.health_every
+                                                                        : nsteps - done;
+    if (int rc = iblb::enqueue_steps(c, n)) return rc;
+    done += n;
+    int hw = 0;
+    if (int rc = read_health(c, &hw)) return rc;
+    if (hw) return health_error(c, hw);
+  }
+  return IBLB_OK;
+}
+
+int iblb_set_health_interval(iblb_ctx *h, int32_t every) {
+  if (!h) return IBLB_EINVAL;
+  if (every < 0) return fail(h->c, IBLB_EINVAL, "the health interval must be >= 0");
+  h->c.health_every = every;
   return IBLB_OK;
 }
 

@@ -177,6 +177,7 @@ struct Ctx {
   int k1_nodes = 0;         // nodes per compute lane of the staged pass, 16-bit (0: default)
   unsigned long long stage_wait_ns = 1000000000ull;  // limit of a staged pass's waits (ns)
   int smem_optin = 0;       // shared memory a block may opt in to (bytes)
+  int health_every = 1000;  // iblb_step reads the health word every this many steps (0: at its end)
   uint64_t config_gen = 0;  // bumped by every call that changes what a queued step launches
   std::string err;
 };

@@ -183,3 +183,12 @@ def test_errors_are_reported():
     with pytest.raises(binding.IBLBError) as e:
         lat.step(1)
     assert e.value.code == binding.IBLB_EUNSTABLE
+    # a long call stops at the end of the health interval in which the check failed
+    lat.set_health_interval(7)
+    done = lat.steps_done
+    with pytest.raises(binding.IBLBError) as e:
+        lat.step(1000)
+    assert e.value.code == binding.IBLB_EUNSTABLE
+    assert lat.steps_done == done + 7
+    with pytest.raises(binding.IBLBError):
+        lat.set_health_interval(-1)
