@@ -67,3 +67,18 @@ def test_no_gpu_fails_loudly():
     from paper_2305_18919_gb300 import binding
     with pytest.raises(binding.IBLBError):
         binding.Lattice(8, 8, 8, 1.0)
+
+
+def test_header_is_plain_c():
+    """include/iblb.h compiles as C99 and as C++ without warnings: the ABI uses plain C types
+    only (no torch or C++ types in the signatures)."""
+    import shutil
+    import subprocess
+    hdr = os.path.join(ROOT, "include", "iblb.h")
+    for cc, args in (("gcc", ["-std=c99", "-x", "c"]), ("g++", ["-std=c++17", "-x", "c++"])):
+        exe = shutil.which(cc)
+        if exe is None:
+            pytest.skip(f"{cc} not installed")
+        r = subprocess.run([exe, *args, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
