@@ -140,3 +140,23 @@ def test_theory_curves():
     # Eq. deformation: alpha = (1, 1, 1) gives 35/48 Ca, (1, 0, 1) gives 5/7 Ca
     assert ob.theory_deformation((1, 1, 1), 0.048) == pytest.approx(0.035, rel=1e-14)
     assert ob.theory_deformation((1, 0, 1), 0.07) == pytest.approx(0.05, rel=1e-14)
+
+
+def test_agrees_with_the_physics_pins_helper():
+    """The numpy helper the oracle's physics pins use (tests/observables.py, written apart
+    from this module) gives the same D, Theta and volume on deformed, turned meshes."""
+    import observables as tob
+    rng = np.random.default_rng(3)
+    for sub, axes, phi in ((2, (1.3, 1.0, 0.8), 0.4), (3, (1.0, 1.1, 1.6), -0.9),
+                           (4, (2.0, 1.0, 1.0), 0.05)):
+        v, f = inputs.icosphere(sub, 5.0, (0.0, 0.0, 0.0))
+        v = rotate_xz(v * np.array(axes), phi) + rng.uniform(-0.05, 0.05, v.shape)
+        v = v + np.array([30.0, 20.0, 12.0])
+        D_ref, th_ref = tob.taylor_deformation(v, np.asarray(f))
+        D, th = ob.deformation(t(v), f)
+        assert float(D) == pytest.approx(D_ref, rel=1e-10)
+        assert float(th) == pytest.approx(th_ref, abs=1e-10)
+        V_ref, c_ref, _ = tob.volume_moments(v, np.asarray(f))
+        V, c, _ = ob.volume_moments(t(v), f)
+        assert float(V) == pytest.approx(V_ref, rel=1e-12)
+        np.testing.assert_allclose(c.numpy(), c_ref, atol=1e-10)
