@@ -32,15 +32,18 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/libiblb_oracle.so`` (plain -O2, IEEE math)."""
+    """Compile the oracle into ``oracle/_build/libiblb_oracle.so`` (plain -O2, IEEE math, no
+    contraction), with OpenMP where the compiler has it (the per-node loops then split over
+    z-planes with identical results; without it the oracle runs in one thread)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
-           _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off"]
+    r = subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], capture_output=True)
+    if r.returncode != 0:
+        subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -74,6 +77,9 @@ def lib():
             L.iblbref_step.argtypes = [_p, _i]
             L.iblbref_read_fields.argtypes = [_p, _dp, _dp]
             L.iblbref_read_populations.argtypes = [_p, _dp]
+            L.iblbref_set_populations.argtypes = [_p, _dp]
+            L.iblbref_set_threads.restype = _i
+            L.iblbref_set_threads.argtypes = [_i]
             L.iblbref_read_vertices.argtypes = [_p, _dp]
             L.iblbref_read_vertex_velocities.argtypes = [_p, _dp]
             L.iblbref_read_forces.argtypes = [_p, _dp, _dp]
@@ -83,6 +89,12 @@ def lib():
             L.iblbref_steps_done.argtypes = [_p]
             _lib = L
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's per-node loops (n <= 0: keep); returns the count in effect.
+    Results do not depend on it."""
+    return int(lib().iblbref_set_threads(int(n)))
 
 
 def _f64(a, shape=None):
@@ -260,6 +272,11 @@ class Simulation:
         f = np.zeros((19, nz, ny, nx))
         self._L.iblbref_read_populations(self.h, _dptr(f))
         return f
+
+    def set_populations(self, f):
+        """Replace the post-streaming populations [19, nz, ny, nx] the next step reads."""
+        nx, ny, nz = self.shape
+        self._L.iblbref_set_populations(self.h, _dptr(_f64(f, (19, nz, ny, nx))))
 
     def vertices(self):
         q = np.zeros((self.nv, 3))

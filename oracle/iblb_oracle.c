@@ -31,12 +31,21 @@
  *  R8  The velocity interpolated to the vertices uses the populations after streaming and
  *      the force field that was spread and used in the same step's collision.
  *  R9  Vertex positions are unwrapped; stencil indices wrap in the periodic directions.
+ *
+ * Threads: built with OpenMP, the three per-node loops of a step (collision, streaming, the
+ * velocity moments) are split over z-planes. Every node's arithmetic is the same as in one
+ * thread and no two threads write the same value (streaming's destinations are distinct), so
+ * the results are identical for any thread count. Forces, spreading, interpolation and every
+ * reduction stay in one thread, in index order.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 19
 static const double CS2 = 1.0 / 3.0;  /* c_s^2 with dx = dt = 1, Sec. III */
@@ -496,6 +505,7 @@ static void sim_step(ref_sim *s) {
     iblbref_spread(nx, ny, nz, s->has_walls, s->nv, s->q, s->phi, s->F);
   }
   /* collision, Eq. 9 right-hand side, with the total force F + g */
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < nz; z++) {
     if (!is_fluid_z(s, z)) continue;
     for (int y = 0; y < ny; y++)
@@ -509,6 +519,7 @@ static void sim_step(ref_sim *s) {
       }
   }
   /* propagation, Eq. 9 left-hand side, with half-way bounce-back at the walls (R7) */
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < nz; z++) {
     if (!is_fluid_z(s, z)) continue;
     for (int y = 0; y < ny; y++)
@@ -527,6 +538,7 @@ static void sim_step(ref_sim *s) {
         }
   }
   /* fluid velocity from the streamed populations with the same force (R8) */
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < nz; z++)
     for (int y = 0; y < ny; y++)
       for (int x = 0; x < nx; x++) {
@@ -580,6 +592,24 @@ void iblbref_read_fields(void *h, double *rho, double *u) {
 void iblbref_read_populations(void *h, double *f) {
   ref_sim *s = (ref_sim *)h;
   memcpy(f, s->f, sizeof(double) * Q * s->ncell);
+}
+
+/* Replace the populations [19][nz][ny][nx] (the post-streaming state the next step reads). */
+void iblbref_set_populations(void *h, const double *f) {
+  ref_sim *s = (ref_sim *)h;
+  memcpy(s->f, f, sizeof(double) * Q * s->ncell);
+}
+
+/* Threads of the per-node loops (see the header); returns the count in effect, 1 without
+   OpenMP. n <= 0 keeps the current setting. */
+int iblbref_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 void iblbref_read_vertices(void *h, double *q) {

@@ -18,8 +18,8 @@ whose first and second moments about o are v s / 4 and v (sum_k p_k p_k^T + s s^
 corners relative to o, s their sum); the sums over the faces are those of the enclosed volume.
 
 The theory curves the paper compares D and Theta with (small deformations) are given as plain
-functions: Eq. deformation (coated droplets and particles), Eq. deformation_droplet (pure droplet)
-and Eq. inclination_angle.
+functions: Eq. deformation (coated droplets and particles), Eq. deformation_droplet (pure droplet),
+Eq. inclination_angle, and the transient of Eq. evJK integrated numerically (bbr_evolution).
 """
 from __future__ import annotations
 
@@ -94,6 +94,59 @@ def theory_deformation_droplet(Ca, lam=1.0):
 def theory_inclination_droplet(Ca, lam=1.0):
     """Inclination angle of a pure droplet at small Ca, Eq. inclination_angle (radians)."""
     return math.pi / 4.0 - (19.0 * lam + 16.0) * (2.0 * lam + 3.0) / (80.0 * (lam + 1.0)) * Ca
+
+
+def bbr_evolution(alpha, Ca, t_end, dt=0.002, lam=1.0, every=1):
+    """Small-deformation shape evolution of Eq. evJK (Sec. II), integrated by classical RK4.
+
+    Returns (t, D, Theta): the time t in units of the inverse shear rate, the deformation index
+    D = (J_11^2 + J_12^2)^(1/2) of Eq. deformation_J and the inclination Theta (radians) of the
+    major axis of J from the flow direction, every `every` steps of dt.
+
+    Reading of the garbled dimensions: time runs in t_hat = gamma_dot t; E and Omega are the
+    symmetric and antisymmetric parts of the velocity gradient of a unit simple shear
+    u = (x_2, 0, 0) (index 1 the flow, 2 the gradient direction; here x and z); the material
+    tensors L and M of Eq. L_M are formed with alpha divided by the alpha of Ca (alpha1 for
+    pre-stressed particles, alpha3 otherwise) and divided by Ca, which makes J of order Ca so
+    that D needs no factor Ca. The Jaumann derivative is dA/dt - (Omega A - A Omega) with
+    Omega_ab = (du_a/dx_b - du_b/dx_a) / 2. J and K start at zero (a sphere at rest).
+    Under this reading the steady state reproduces Eq. deformation (coated droplets and
+    capsules), Eq. deformation_droplet and, for a droplet, Eq. inclination_angle.
+    """
+    a = np.asarray(alpha, dtype=np.float64)
+    ref = a[0] if a[0] > 0 else a[2]
+    a1, a2, a3 = a / ref
+    E = np.zeros((3, 3))
+    E[0, 2] = E[2, 0] = 0.5
+    W = np.zeros((3, 3))
+    W[0, 2], W[2, 0] = 0.5, -0.5
+    c1 = 1.0 / (2.0 * lam + 3.0)
+    c2 = (6.0 * lam + 4.0) / ((2.0 * lam + 3.0) * (19.0 * lam + 16.0))
+    c3 = 2.0 / (19.0 * lam + 16.0)
+
+    def rates(J, K):
+        L = (4.0 * (a2 + a3) * J - (6.0 * a2 + 10.0 * a3) * K) / Ca
+        M = (-4.0 * (a1 + 2.0 * a2 + 2.0 * a3) * J + (12.0 * a2 + 16.0 * a3) * K) / Ca
+        dK = W @ K - K @ W + c1 * (5.0 * E + L) + c2 * M
+        dJK = W @ (J - K) - (J - K) @ W + c3 * M
+        return dK + dJK, dK
+
+    J = np.zeros((3, 3))
+    K = np.zeros((3, 3))
+    n = int(round(t_end / dt))
+    ts, Ds, Th = [0.0], [0.0], [math.pi / 4.0]
+    for k in range(1, n + 1):
+        j1, k1 = rates(J, K)
+        j2, k2 = rates(J + 0.5 * dt * j1, K + 0.5 * dt * k1)
+        j3, k3 = rates(J + 0.5 * dt * j2, K + 0.5 * dt * k2)
+        j4, k4 = rates(J + dt * j3, K + dt * k3)
+        J = J + dt / 6.0 * (j1 + 2.0 * j2 + 2.0 * j3 + j4)
+        K = K + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        if k % every == 0:
+            ts.append(k * dt)
+            Ds.append(math.hypot(J[0, 0], J[0, 2]))
+            Th.append(0.5 * math.atan2(2.0 * J[0, 2], J[0, 0] - J[2, 2]))
+    return np.array(ts), np.array(Ds), np.array(Th)
 
 
 def contact_angle(q, faces, z_wall=0.5, exclude=1.0, select=None):

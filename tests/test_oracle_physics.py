@@ -1,14 +1,23 @@
 """Whole-step pins of the oracle against the paper's small-deformation shear-flow theory
-(Sec. IV): steady Taylor deformation of a pure droplet (Eq. 22), of a rigidly coated
-droplet (Eq. 21), linearity of D in Ca, and the Chaffey-Brenner inclination (Eq. 23).
+(Sec. IV) at a true steady state.
 
-Workload: the 32^3 shear box (walls at -/+0.01, tau = 1, R = 6, subdivision 3), started
-from the linear Couette profile. At R/H = 0.2 wall confinement raises D above the
-unbounded theory; the absolute bound is therefore one-sided and loose, while the ratios
-(which confinement affects alike) are tight.
+Workload: the 32^3 shear box (walls at -/+0.01, tau = 1, R = 6, subdivision 3), started from
+the linear Couette profile, with a coated particle instead of the pure droplet: a droplet's
+membrane resists no tangential distortion and at this resolution it never settles (its D
+keeps growing), while the coated particles are steady after about 1250 steps. Each run is
+shown to be steady first (D changes by less than 5e-4 over the last 20 % of 2000 steps);
+then D is held against Eq. deformation, its scaling with Ca, and the inclination against the
+steady state of Eq. evJK (observables.bbr_evolution), which for coated particles is the
+theory's only statement on Theta.
+
+Measured: D = 1.17 (rigidly coated) and 1.08 (softly coated) times Eq. deformation at
+Ca = 0.067, 1.18 and 1.08 at Ca = 0.033 (box confinement at R/H = 0.2 and the width of the
+delta stencil raise D; both scale out of the ratio), D(Ca/2)/D(Ca) = 0.504 and 0.502 against
+0.502, and Theta within 0.4 degrees of Eq. evJK's steady inclination.
 """
 import concurrent.futures as cf
 import math
+import os
 
 import numpy as np
 import pytest
@@ -16,28 +25,38 @@ import pytest
 from observables import taylor_deformation
 from pairs import shear_profile
 from paper_2305_18919_gb300 import inputs
+from paper_2305_18919_gb300 import observables as ob
+
+STEPS, SAMPLE = 2000, 100
 
 
-def _run(alpha, steps):
+def _run(cls, abar, threads):
     import oracle
+    oracle.set_threads(threads)
     wl = inputs.shear_32_fp64()
-    wl.alpha = alpha
+    wl.alpha = tuple(abar * a for a in inputs.ALPHA_CLASSES[cls])
     s = oracle.Simulation.from_workload(wl)
     s.init_equilibrium(*shear_profile(wl))
-    s.step(steps)
-    v, f = wl.mesh()
-    D, theta = taylor_deformation(s.vertices(), f)
+    _, f = wl.mesh()
+    Ds, ths = [], []
+    for k in range(STEPS // SAMPLE):
+        s.step(SAMPLE)
+        if (k + 1) * SAMPLE >= 0.8 * STEPS:
+            D, th = taylor_deformation(s.vertices(), f)
+            Ds.append(D)
+            ths.append(th)
     V, V0 = s.volume()
     s.close()
-    return D, theta, V / V0 - 1
+    return np.array(Ds), np.array(ths), V / V0 - 1
 
 
 @pytest.fixture(scope="module")
 def shear_results(oracle_mod):
-    jobs = {"droplet": ((0.01, 0, 0), 1000), "droplet_stiff": ((0.02, 0, 0), 600),
-            "rigid": ((0.01, 0.01, 0.01), 600)}
-    with cf.ThreadPoolExecutor(3) as ex:  # ctypes calls release the GIL
-        futs = {k: ex.submit(_run, *v) for k, v in jobs.items()}
+    jobs = {"rigid": ("rigidly_coated", 0.01), "soft": ("softly_coated", 0.01),
+            "rigid_half_ca": ("rigidly_coated", 0.02)}
+    threads = max(1, (os.cpu_count() or 1) // len(jobs))
+    with cf.ThreadPoolExecutor(len(jobs)) as ex:  # ctypes calls release the GIL
+        futs = {k: ex.submit(_run, *v, threads) for k, v in jobs.items()}
         return {k: f.result() for k, f in futs.items()}
 
 
@@ -49,31 +68,42 @@ def _ca(alpha1):
 
 
 @pytest.mark.slow
-def test_droplet_deformation_and_inclination(shear_results):
-    D, theta, dV = shear_results["droplet"]
+@pytest.mark.parametrize("key", ["rigid", "soft", "rigid_half_ca"])
+def test_coated_particle_is_steady(shear_results, key):
+    D, th, dV = shear_results[key]
+    assert np.ptp(D) < 5e-4
+    assert np.ptp(th) < math.radians(0.2)
+    assert abs(dV) < 1e-2
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("key,cls", [("rigid", "rigidly_coated"), ("soft", "softly_coated")])
+def test_steady_deformation_near_eq_deformation(shear_results, key, cls):
+    """Eq. deformation with alpha = abar(1,1,1) gives 35/48 Ca, with abar(1,0,1) 20/28 Ca;
+    confinement and the stencil's width put the measured D above it, by less than 25 %."""
     Ca = _ca(0.01)
-    D_theory = (19 + 16) / (16 + 16) * Ca               # Eq. 22, lambda = 1
-    theta_theory = math.pi / 4 - (35 * 5) / (80 * 2) * Ca  # Eq. 23, lambda = 1
-    assert D_theory < D < 1.4 * D_theory
-    assert abs(theta - theta_theory) < math.radians(1.5)
-    assert abs(dV) < 5e-3
+    D_theory = ob.theory_deformation(inputs.ALPHA_CLASSES[cls], Ca)
+    assert 1.0 < shear_results[key][0][-1] / D_theory < 1.25
 
 
 @pytest.mark.slow
 def test_deformation_linear_in_capillary_number(shear_results):
-    D1 = shear_results["droplet"][0]
-    D2 = shear_results["droplet_stiff"][0]
-    assert abs(D2 / D1 - 0.5) < 0.04
+    """Doubling alpha halves Ca; Eq. evJK's steady D then drops by 0.502 (the O(Ca^2) term)."""
+    Ca = _ca(0.01)
+    _, D1, _ = ob.bbr_evolution((1, 1, 1), Ca, 4.0, dt=1e-3, every=4000)
+    _, D2, _ = ob.bbr_evolution((1, 1, 1), Ca / 2, 4.0, dt=1e-3, every=4000)
+    ratio = shear_results["rigid_half_ca"][0][-1] / shear_results["rigid"][0][-1]
+    assert abs(ratio - D2[-1] / D1[-1]) < 0.02
 
 
 @pytest.mark.slow
-def test_rigidly_coated_to_droplet_ratio(shear_results):
-    """Eq. 21 with alpha = abar(1,1,1) gives D = 35/48 Ca; Eq. 22 gives 35/32 Ca: ratio 2/3."""
-    a1 = a2 = a3 = 1.0
-    coef = 5 * a1 * (3 * a2 + 4 * a3) / (4 * (3 * a1 * a2 + 5 * a1 * a3 + 2 * a2 * a3 + 2 * a3 ** 2))
-    assert abs(coef - 35 / 48) < 1e-15
-    ratio = shear_results["rigid"][0] / shear_results["droplet"][0]
-    assert abs(ratio / (coef / (35 / 32)) - 1) < 0.1
+@pytest.mark.parametrize("key,cls,abar", [("rigid", "rigidly_coated", 0.01),
+                                          ("soft", "softly_coated", 0.01),
+                                          ("rigid_half_ca", "rigidly_coated", 0.02)])
+def test_inclination_matches_the_steady_state_of_eq_evjk(shear_results, key, cls, abar):
+    _, _, th_theory = ob.bbr_evolution(inputs.ALPHA_CLASSES[cls], _ca(abar), 4.0, dt=1e-3,
+                                       every=4000)
+    assert abs(shear_results[key][1][-1] - th_theory[-1]) < math.radians(1.0)
 
 
 def test_capsule_at_rest_stays_at_rest(oracle_mod):
