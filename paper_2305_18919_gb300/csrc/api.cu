@@ -342,7 +342,7 @@ void iblb_destroy(iblb_ctx *h) {
     dfree(c.out_src[b]);
     dfree(c.Fslot[b]);
   }
-  dfree(c.counters); dfree(c.slot_count); dfree(c.src_index); dfree(c.Rslot); dfree(c.bucket); dfree(c.overflow); dfree(c.Uslot);
+  dfree(c.counters); dfree(c.slot_count); dfree(c.src_index); dfree(c.Rslot); dfree(c.bucket); dfree(c.spill_bits); dfree(c.Uslot);
   dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.xref); dfree(c.fgeo); dfree(c.disp); dfree(c.vf_start); dfree(c.vf_list);
   dfree(c.fcontrib); dfree(c.fnorm); dfree(c.vol_partial); dfree(c.phi); dfree(c.gvol); dfree(c.stencil);
   dfree(c.dscratch);
@@ -441,7 +441,9 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
   c.max_sources = nv < c.max_slots ? nv : c.max_slots;  // a source tile holds >= 1 vertex base
   CUDA_TRY(c, dalloc_bytes(&c.Rslot, (size_t)c.max_sources * 343 * 4 * rs));
   CUDA_TRY(c, dalloc(&c.bucket, (size_t)c.max_slots * iblb::BUCKET_CAP));
-  CUDA_TRY(c, dalloc(&c.overflow, (size_t)nv));
+  c.spill_words = (nv + 31) / 32;
+  CUDA_TRY(c, dalloc(&c.spill_bits, (size_t)c.spill_words));
+  CUDA_TRY(c, cudaMemsetAsync(c.spill_bits, 0, (size_t)c.spill_words * sizeof(unsigned), c.stream));
   CUDA_TRY(c, dalloc_bytes(&c.Uslot, (size_t)c.max_slots * 4 * iblb::TILE_CELLS * rs));
   CUDA_TRY(c, cudaMemsetAsync(c.counters, 0, 8 * sizeof(int), c.stream));
   CUDA_TRY(c, cudaMemsetAsync(c.qdot, 0, (size_t)3 * nv * sizeof(double), c.stream));

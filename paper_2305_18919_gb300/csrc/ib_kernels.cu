@@ -90,6 +90,8 @@ struct FaceArgs {
   const int *other_slot_tile, *other_nslots;
   int reset;
   int *ovf_count;
+  unsigned *spill_bits;  // [spill_words] cleared here, before the vertex kernel bins
+  int spill_words;
 };
 
 // K3a for block `bid` of `nb` (the single-context kernel and the batched one share it).
@@ -193,9 +195,11 @@ __device__ __forceinline__ void face_body(const FaceArgs<real> &A, int bid, int 
     if (threadIdx.x == 0) vol_partial[bid] = v;
   }
   if (bid == 0 && threadIdx.x == 0) {
-    A.ovf_count[0] = 0;  // overflow list length
+    A.ovf_count[0] = 0;  // vertices beyond their bucket (a count only)
     A.ovf_count[2] = 0;  // number of source tiles (counters[4])
   }
+  for (int w = bid * blockDim.x + threadIdx.x; w < A.spill_words; w += nb * blockDim.x)
+    A.spill_bits[w] = 0u;
   if (A.reset) {
     const int n_other = min(*A.other_nslots, D.max_slots);
     for (int s = bid * blockDim.x + threadIdx.x; s < n_other; s += nb * blockDim.x)
@@ -260,7 +264,8 @@ struct VertexArgs {
   StencilRec<real> *stencil;
   int bin;
   const int *tile_slot;
-  int *slot_count, *bucket, *overflow, *ovf_count, *src_index, *nsources, *health, *zero_counter;
+  int *slot_count, *bucket, *ovf_count, *src_index, *nsources, *health, *zero_counter;
+  unsigned *spill_bits;  // bit i: vertex i did not fit in its tile's bucket
   Dims D;
 };
 
@@ -323,8 +328,10 @@ __device__ __forceinline__ void vertex_body(const VertexArgs<real> &A, int bid) 
   if (rank < BUCKET_CAP) {
     A.bucket[(size_t)s * BUCKET_CAP + rank] = i;
   } else {
-    const int o = atomicAdd(A.ovf_count, 1);
-    A.overflow[o] = i;
+    // which vertices end up in the bucket depends on the order of the atomics; the spread
+    // pass therefore adds every vertex of a tile that spilled in vertex-index order
+    atomicAdd(A.ovf_count, 1);
+    atomicOr(&A.spill_bits[i >> 5], 1u << (i & 31));
   }
 }
 
@@ -367,12 +374,15 @@ __device__ __forceinline__ real pick4(const real w[4], int d) {
 // and the vertices are then added one after another into the 7x7x7 region of S, each lane
 // adding two of the 64 stencil nodes of a vertex (distinct nodes, so no atomics). The region
 // is written out and its index pushed to the (up to 8) tiles T = S + {0,1}^3 it overlaps.
-// Vertices in the overflow list (more than 64 in a tile) follow in list order. The order of
-// summation is fixed by the sorted buckets.
+// A tile with more than 64 vertices (its bucket holds 64 of them, chosen by the order of the
+// binning atomics) marks its bucket's vertices in the spill bitmap, which already holds its
+// spilled ones, and adds all of its vertices in increasing vertex index instead, found by a
+// scan of the bitmap. Either way the order of summation depends only on the vertex set.
 template <typename real>
 struct SourceArgs {
-  const int *tile_slot, *slot_tile, *nslots_ptr, *slot_count, *src_index, *bucket, *overflow,
-      *ovf_count_ptr;
+  const int *tile_slot, *slot_tile, *nslots_ptr, *slot_count, *src_index, *bucket;
+  unsigned *spill_bits;
+  int spill_words;
   const StencilRec<real> *stencil;
   const Vec4<real> *phi, *gvol;
   const double *vol_partial;
@@ -390,7 +400,7 @@ __device__ __forceinline__ void spread_source_body(const SourceArgs<real> &A, in
   const int *__restrict__ slot_count = A.slot_count;
   const int *__restrict__ src_index = A.src_index;
   const int *__restrict__ bucket = A.bucket;
-  const int *__restrict__ overflow = A.overflow;
+  unsigned *spill_bits = A.spill_bits;
   const StencilRec<real> *__restrict__ stencil = A.stencil;
   const Vec4<real> *__restrict__ phi = A.phi;
   const Vec4<real> *__restrict__ gvol = A.gvol;
@@ -403,7 +413,6 @@ __device__ __forceinline__ void spread_source_body(const SourceArgs<real> &A, in
   __shared__ Vec4<real> s_f[W][BUCKET_CAP];
   __shared__ int s_b[W][BUCKET_CAP][3];
   const int nslots = min(*A.nslots_ptr, D.max_slots);
-  const int novf = *A.ovf_count_ptr;
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   double V;
   const real coef = (real)volume_coef(A.vol_partial, vp.vol_blocks, vp.V0, vp.kV, vp.volume_on, &V);
@@ -416,7 +425,6 @@ __device__ __forceinline__ void spread_source_body(const SourceArgs<real> &A, in
     const int cnt = slot_count[s];
     if (cnt == 0) continue;  // no vertex has its base node here: no region
     const int n = min(cnt, BUCKET_CAP);
-    const int nspill = cnt > BUCKET_CAP ? novf : 0;  // scan the overflow list only if it spilled
     const int t = slot_tile[s];
     const int tsx = t % D.ntx, tsy = (t / D.ntx) % D.nty, tsz = t / (D.ntx * D.nty);
     const int Sx = tsx * TILE, Sy = tsy * TILE, Sz = tsz * TILE;
@@ -436,71 +444,97 @@ __device__ __forceinline__ void spread_source_body(const SourceArgs<real> &A, in
         if (slot_t >= 0) out_src[8 * (size_t)slot_t + lane] = reg;
       }
     }
-    // sort the bucket by vertex index and stage the records in that order
     const int *bk = bucket + (size_t)s * BUCKET_CAP;
-    const int v0 = lane < n ? bk[lane] : 0x7fffffff;
-    const int v1 = lane + 32 < n ? bk[lane + 32] : 0x7fffffff;
-    int r0 = 0, r1 = 0;
-    for (int m = 0; m < n; m++) {
-      const int vm = __shfl_sync(0xffffffffu, m < 32 ? v0 : v1, m & 31);
-      r0 += vm < v0;
-      r1 += vm < v1;
-    }
-    for (int h = 0; h < 2; h++) {
-      const int v = h ? v1 : v0;
-      const int r = h ? r1 : r0;
-      if ((h ? lane + 32 : lane) >= n) continue;
-      const StencilRec<real> rec = stencil[v];
-      const Vec4<real> pv = phi[v], gv = gvol[v];
-      for (int k = 0; k < 4; k++) {
-        s_w[wq][r][k] = rec.w[0][k];
-        s_w[wq][r][4 + k] = rec.w[1][k];
-        s_w[wq][r][8 + k] = rec.w[2][k];
+    if (cnt <= BUCKET_CAP) {
+      // sort the bucket by vertex index and stage the records in that order
+      const int v0 = lane < n ? bk[lane] : 0x7fffffff;
+      const int v1 = lane + 32 < n ? bk[lane + 32] : 0x7fffffff;
+      int r0 = 0, r1 = 0;
+      for (int m = 0; m < n; m++) {
+        const int vm = __shfl_sync(0xffffffffu, m < 32 ? v0 : v1, m & 31);
+        r0 += vm < v0;
+        r1 += vm < v1;
       }
-      s_f[wq][r] = Vec4<real>{pv.x - coef * gv.x, pv.y - coef * gv.y, pv.z - coef * gv.z, real(0)};
-      // base relative to S_lo (x, y wrapped into [0, n) by the vertex kernel)
-      s_b[wq][r][0] = rec.base[0] - Sx;
-      s_b[wq][r][1] = rec.base[1] - Sy;
-      s_b[wq][r][2] = rec.base[2] - Sz;
-    }
-    for (int k = lane; k < REGION_NODES; k += 32) region[k] = Vec4<real>{0, 0, 0, 0};
-    __syncwarp();
-    for (int c = 0; c < n; c++) {
-      const int bx = s_b[wq][c][0], by = s_b[wq][c][1], bz = s_b[wq][c][2];
-      const Vec4<real> f = s_f[wq][c];
-      const real wxy = s_w[wq][c][dxa] * s_w[wq][c][4 + dya];
       for (int h = 0; h < 2; h++) {
-        const int dz = dza + 2 * h;  // node lane + 32 h has the same dx, dy and dz + 2
-        const int rz = bz + dz;
-        if (rz < 0 || rz >= REGION) continue;  // beyond the lattice in z
-        const real w = wxy * s_w[wq][c][8 + dz];
-        Vec4<real> &o = region[(rz * REGION + by + dya) * REGION + bx + dxa];
-        o.x += w * f.x;
-        o.y += w * f.y;
-        o.z += w * f.z;
+        const int v = h ? v1 : v0;
+        const int r = h ? r1 : r0;
+        if ((h ? lane + 32 : lane) >= n) continue;
+        const StencilRec<real> rec = stencil[v];
+        const Vec4<real> pv = phi[v], gv = gvol[v];
+        for (int k = 0; k < 4; k++) {
+          s_w[wq][r][k] = rec.w[0][k];
+          s_w[wq][r][4 + k] = rec.w[1][k];
+          s_w[wq][r][8 + k] = rec.w[2][k];
+        }
+        s_f[wq][r] = Vec4<real>{pv.x - coef * gv.x, pv.y - coef * gv.y, pv.z - coef * gv.z, real(0)};
+        // base relative to S_lo (x, y wrapped into [0, n) by the vertex kernel)
+        s_b[wq][r][0] = rec.base[0] - Sx;
+        s_b[wq][r][1] = rec.base[1] - Sy;
+        s_b[wq][r][2] = rec.base[2] - Sz;
       }
+      for (int k = lane; k < REGION_NODES; k += 32) region[k] = Vec4<real>{0, 0, 0, 0};
       __syncwarp();
-    }
-    for (int c = 0; c < nspill; c++) {  // vertices spilled from this tile's bucket
-      const int v = overflow[c];
-      const StencilRec<real> rec = stencil[v];
-      const int bzc = min(max(rec.base[2], 0), D.nz - 1);
-      const int bx = rec.base[0] - Sx, by = rec.base[1] - Sy, bz = rec.base[2] - Sz;
-      if (bx < 0 || bx > 3 || by < 0 || by > 3 || (bzc >> 2) * TILE != Sz) continue;
-      const Vec4<real> pv = phi[v], gv = gvol[v];
-      const real fx = pv.x - coef * gv.x, fy = pv.y - coef * gv.y, fz = pv.z - coef * gv.z;
-      const real wxy = pick4(rec.w[0], dxa) * pick4(rec.w[1], dya);
-      for (int h = 0; h < 2; h++) {
-        const int dz = dza + 2 * h;
-        const int rz = bz + dz;
-        if (rz < 0 || rz >= REGION) continue;
-        const real w = wxy * pick4(rec.w[2], dz);
-        Vec4<real> &o = region[(rz * REGION + by + dya) * REGION + bx + dxa];
-        o.x += w * fx;
-        o.y += w * fy;
-        o.z += w * fz;
+      for (int c = 0; c < n; c++) {
+        const int bx = s_b[wq][c][0], by = s_b[wq][c][1], bz = s_b[wq][c][2];
+        const Vec4<real> f = s_f[wq][c];
+        const real wxy = s_w[wq][c][dxa] * s_w[wq][c][4 + dya];
+        for (int h = 0; h < 2; h++) {
+          const int dz = dza + 2 * h;  // node lane + 32 h has the same dx, dy and dz + 2
+          const int rz = bz + dz;
+          if (rz < 0 || rz >= REGION) continue;  // beyond the lattice in z
+          const real w = wxy * s_w[wq][c][8 + dz];
+          Vec4<real> &o = region[(rz * REGION + by + dya) * REGION + bx + dxa];
+          o.x += w * f.x;
+          o.y += w * f.y;
+          o.z += w * f.z;
+        }
+        __syncwarp();
       }
+    } else {
+      // the tile spilled: mark its bucket's vertices too, then add every vertex of the tile in
+      // increasing index (bitmap words read through L2, where the atomics are performed)
+      atomicOr(&spill_bits[bk[lane] >> 5], 1u << (bk[lane] & 31));
+      atomicOr(&spill_bits[bk[lane + 32] >> 5], 1u << (bk[lane + 32] & 31));
+      for (int k = lane; k < REGION_NODES; k += 32) region[k] = Vec4<real>{0, 0, 0, 0};
       __syncwarp();
+      for (int wb = 0; wb < A.spill_words; wb += 32) {
+        const unsigned word_l = wb + lane < A.spill_words ? __ldcg(&spill_bits[wb + lane]) : 0u;
+        unsigned nonzero = __ballot_sync(0xffffffffu, word_l != 0u);
+        while (nonzero) {
+          const int l = __ffs(nonzero) - 1;
+          nonzero &= nonzero - 1;
+          const unsigned word = __shfl_sync(0xffffffffu, word_l, l);
+          const int vl = (wb + l) * 32 + lane;  // this lane's vertex of the word
+          bool mine = false;
+          if ((word >> lane) & 1u) {
+            const StencilRec<real> rl = stencil[vl];
+            const int bzc = min(max(rl.base[2], 0), D.nz - 1);
+            mine = (rl.base[0] >> 2) == tsx && (rl.base[1] >> 2) == tsy && (bzc >> 2) == tsz;
+          }
+          unsigned members = __ballot_sync(0xffffffffu, mine);
+          while (members) {  // the tile's vertices of this word, in index order
+            const int b = __ffs(members) - 1;
+            members &= members - 1;
+            const int v = (wb + l) * 32 + b;
+            const StencilRec<real> rec = stencil[v];
+            const int bx = rec.base[0] - Sx, by = rec.base[1] - Sy, bz = rec.base[2] - Sz;
+            const Vec4<real> pv = phi[v], gv = gvol[v];
+            const real fx = pv.x - coef * gv.x, fy = pv.y - coef * gv.y, fz = pv.z - coef * gv.z;
+            const real wxy = pick4(rec.w[0], dxa) * pick4(rec.w[1], dya);
+            for (int h = 0; h < 2; h++) {
+              const int dz = dza + 2 * h;
+              const int rz = bz + dz;
+              if (rz < 0 || rz >= REGION) continue;
+              const real w = wxy * pick4(rec.w[2], dz);
+              Vec4<real> &o = region[(rz * REGION + by + dya) * REGION + bx + dxa];
+              o.x += w * fx;
+              o.y += w * fy;
+              o.z += w * fz;
+            }
+            __syncwarp();
+          }
+        }
+      }
     }
     Vec4<real> *out = A.Rslot + (size_t)reg * REGION_NODES;
     for (int k = lane; k < REGION_NODES; k += 32) out[k] = region[k];
@@ -646,6 +680,62 @@ __device__ __forceinline__ void mark_tile(const AxisTiles ax[3], int e, const Di
 // sums the 16 nodes of its z-plane of the stencil, the 4 planes are summed by shuffles and
 // the update is added to the double position. Each lane then marks two of the (up to 8)
 // tiles of the new position in the other map.
+// The delta-weight accumulation of a vertex is carried at double precision in every
+// precision (VertexSum): each stencil row's four products w_x u (one x row of a tile, in the
+// arithmetic type) is added to the vertex's sum with its weight w_y w_z, and the four planes'
+// sums are added across the lanes, without rounding the sum back to float.
+template <typename real>
+struct VertexSum;
+
+// FP64 contexts: a plain double sum.
+template <>
+struct VertexSum<double> {
+  double s[3] = {0.0, 0.0, 0.0};
+  __device__ __forceinline__ void add_prod(int k, double a, double b) { s[k] += a * b; }
+  __device__ __forceinline__ void set(int k, double x) { s[k] = x; }
+  __device__ __forceinline__ void add_lanes(int o) {
+    for (int k = 0; k < 3; k++) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+  }
+  __device__ __forceinline__ double value(int k) const { return s[k]; }
+};
+
+// Float contexts: the sum is a pair of floats hi + lo (double-float arithmetic), kept exact
+// up to rounding at about 2^-44 of the sum with the error-free transformations of Dekker
+// (the product a b = p + e, e by a fused multiply-add) and Knuth (TwoSum: s + err = x + y).
+// This is as accurate as a double sum of the same float products; on GB300 double arithmetic
+// runs at 1/64 of the float rate, and the double form lengthened the 16-bit step. The _rn
+// intrinsics keep the compiler from fusing the steps the transformations rely on.
+template <>
+struct VertexSum<float> {
+  float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+  __device__ __forceinline__ void add(int k, float x, float xerr) {
+    const float s = __fadd_rn(hi[k], x);
+    const float bp = __fsub_rn(s, hi[k]);
+    const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi[k] = s;
+    lo[k] = __fadd_rn(lo[k], __fadd_rn(err, xerr));
+  }
+  __device__ __forceinline__ void add_prod(int k, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    add(k, p, __fmaf_rn(a, b, -p));
+  }
+  __device__ __forceinline__ void set(int k, double x) {
+    hi[k] = __double2float_rn(x);
+    lo[k] = __double2float_rn(x - (double)hi[k]);
+  }
+  // the same result in every lane of the butterfly: the addition is commutative and TwoSum's
+  // error term is exact
+  __device__ __forceinline__ void add_lanes(int o) {
+    for (int k = 0; k < 3; k++) {
+      const float h = __shfl_xor_sync(0xffffffffu, hi[k], o);
+      const float l = __shfl_xor_sync(0xffffffffu, lo[k], o);
+      lo[k] = __fadd_rn(lo[k], l);
+      add(k, h, 0.f);
+    }
+  }
+  __device__ __forceinline__ double value(int k) const { return (double)hi[k] + (double)lo[k]; }
+};
+
 template <typename real>
 struct InterpArgs {
   int nv;
@@ -678,7 +768,7 @@ __device__ __forceinline__ void interp_body(const InterpArgs<real> &A, int bid) 
   const int v = gid >> 2;
   const int dz = gid & 3;
   const bool valid = v < nv;
-  real acc[3] = {0, 0, 0};
+  VertexSum<real> acc;
   if (valid) {
     const StencilRec<real> rec = stencil[v];
     int Z = rec.base[2] + dz;
@@ -687,11 +777,13 @@ __device__ __forceinline__ void interp_body(const InterpArgs<real> &A, int bid) 
       const real wz = pick4(rec.w[2], dz);
       if (D.has_walls && (Z == 0 || Z == D.nz - 1)) {
         const double3 w = Z == 0 ? ub : ut;
-        const real sxy = (rec.w[0][0] + rec.w[0][1] + rec.w[0][2] + rec.w[0][3]) *
-                         (rec.w[1][0] + rec.w[1][1] + rec.w[1][2] + rec.w[1][3]) * wz;
-        acc[0] = sxy * (real)w.x;
-        acc[1] = sxy * (real)w.y;
-        acc[2] = sxy * (real)w.z;
+        const double sxy =
+            ((double)rec.w[0][0] + (double)rec.w[0][1] + (double)rec.w[0][2] + (double)rec.w[0][3]) *
+            ((double)rec.w[1][0] + (double)rec.w[1][1] + (double)rec.w[1][2] + (double)rec.w[1][3]) *
+            (double)wz;
+        acc.set(0, sxy * w.x);
+        acc.set(1, sxy * w.y);
+        acc.set(2, sxy * w.z);
       } else {
         // the 4 stencil nodes along x (and along y) fall in at most two tiles: look up the
         // (up to) four tile slots of this z-plane once
@@ -723,25 +815,27 @@ __device__ __forceinline__ void interp_body(const InterpArgs<real> &A, int bid) 
             r3[2] += w * u.z;
           }
           const real wyz = rec.w[1][dy] * wz;
-          acc[0] += wyz * r3[0];
-          acc[1] += wyz * r3[1];
-          acc[2] += wyz * r3[2];
+          acc.add_prod(0, wyz, r3[0]);
+          acc.add_prod(1, wyz, r3[1]);
+          acc.add_prod(2, wyz, r3[2]);
         }
       }
     }
   }
   // sum of the 4 planes (fixed butterfly order)
-  for (int o = 2; o > 0; o >>= 1)
-    for (int k = 0; k < 3; k++) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  for (int o = 2; o > 0; o >>= 1) acc.add_lanes(o);
   if (valid) {
-    double pn[3];
-    for (int k = 0; k < 3; k++) pn[k] = q[3 * (size_t)v + k] + (double)acc[k];
+    double pn[3], qd[3];
+    for (int k = 0; k < 3; k++) {
+      qd[k] = acc.value(k);
+      pn[k] = q[3 * (size_t)v + k] + qd[k];
+    }
     if (dz == 0) {
       int h = 0;
       for (int k = 0; k < 3; k++) {
-        qdot[3 * (size_t)v + k] = (double)acc[k];
+        qdot[3 * (size_t)v + k] = qd[k];
         q[3 * (size_t)v + k] = pn[k];
-        if (!(fabs((double)acc[k]) < 0.1)) h |= (acc[k] == acc[k]) ? H_FAST : H_NAN;
+        if (!(fabs(qd[k]) < 0.1)) h |= (qd[k] == qd[k]) ? H_FAST : H_NAN;
       }
       if (D.has_walls && (pn[2] - D.zb < 0.05 || D.zt - pn[2] < 0.05)) h |= H_WALL;
       if (h) atomicOr(health, h);
@@ -898,6 +992,8 @@ FaceArgs<real> face_args(const Ctx &c, int reset) {
   a.other_nslots = c.counters + other;
   a.reset = reset;
   a.ovf_count = c.counters + 2;
+  a.spill_bits = c.spill_bits;
+  a.spill_words = c.spill_words;
   return a;
 }
 int face_blocks(const Ctx &c) { return c.vol_blocks; }
@@ -918,8 +1014,8 @@ VertexArgs<real> vertex_args(const Ctx &c, int bin) {
   a.tile_slot = c.tile_slot[c.map];
   a.slot_count = c.slot_count;
   a.bucket = c.bucket;
-  a.overflow = c.overflow;
   a.ovf_count = c.counters + 2;
+  a.spill_bits = c.spill_bits;
   a.src_index = c.src_index;
   a.nsources = c.counters + 4;
   a.health = c.counters + 3;
@@ -938,8 +1034,8 @@ SourceArgs<real> source_args(const Ctx &c) {
   a.slot_count = c.slot_count;
   a.src_index = c.src_index;
   a.bucket = c.bucket;
-  a.overflow = c.overflow;
-  a.ovf_count_ptr = c.counters + 2;
+  a.spill_bits = c.spill_bits;
+  a.spill_words = c.spill_words;
   a.stencil = (const StencilRec<real> *)c.stencil;
   a.phi = (const Vec4<real> *)c.phi;
   a.gvol = (const Vec4<real> *)c.gvol;

@@ -38,7 +38,7 @@ __host__ __device__ constexpr double wgt(int i) {
 // 4x4x4 delta stencil ("active" tiles) carry force and velocity buffers.
 constexpr int TILE = 4;
 constexpr int TILE_CELLS = TILE * TILE * TILE;
-// vertices per source-tile bucket before they spill to the overflow list
+// vertices per source-tile bucket; the rest of a fuller tile is marked in a spill bitmap
 constexpr int BUCKET_CAP = 64;
 
 // Health word bits (read back by iblb_step).
@@ -125,14 +125,16 @@ struct Ctx {
   int tile_estimate = 0;  // active tiles expected for the mesh (sizes the batched grids)
   int *tile_slot[2] = {nullptr, nullptr};  // [ntiles] slot or -1
   int *slot_tile[2] = {nullptr, nullptr};  // [max_slots] tile id of each active slot
-  int *counters = nullptr;  // [0..1] nslots per map, [2] overflow count, [3] health, [4] sources
+  int *counters = nullptr;  // [0..1] nslots per map, [2] spilled vertices, [3] health, [4] sources
   int *src_index = nullptr;                // [max_slots] region of a source tile (slot)
   void *Rslot = nullptr;                   // [max_sources][343] Vec4 spreading regions
   int *out_src[2] = {nullptr, nullptr};    // per map: [max_slots][8] region of source T - e
   int max_sources = 0;
   int *slot_count = nullptr;               // [max_slots] vertices in each source bucket
   int *bucket = nullptr;                   // [max_slots][BUCKET_CAP]
-  int *overflow = nullptr;                 // [nv] vertices not fitting in their bucket
+  unsigned *spill_bits = nullptr;          // [spill_words] bit v: vertex v did not fit in its
+                                           //   tile's bucket (cleared by every face pass)
+  int spill_words = 0;                     // (nv + 31) / 32
   void *Fslot[2] = {nullptr, nullptr};     // per map: [max_slots][64] Vec4 force density
   void *Uslot = nullptr;                   // [max_slots][64] Vec4 velocity
   int map = 0;                             // tile map of the current vertex positions
