@@ -199,10 +199,11 @@ __global__ void adj_face_tangent_kernel(FaceArgs A, const double *__restrict__ q
   }
 }
 
-// Fixed-order sums over faces (one block): out[0] = sum a, out[1..m] = sums of b's columns.
+// Fixed-order sums over faces (one block): out[0] = sum a, out[1..m] = sums of b's columns;
+// with grad, the b sums (the parameter derivatives of the step) are also added to grad[0..m-1].
 __global__ void adj_face_sums_kernel(int nf, const double *__restrict__ a,
                                      const double *__restrict__ b, int m,
-                                     double *__restrict__ out) {
+                                     double *__restrict__ out, double *__restrict__ grad) {
   __shared__ double sh[256][5];
   const int t = threadIdx.x;
   double acc[5] = {0, 0, 0, 0, 0};
@@ -217,8 +218,11 @@ __global__ void adj_face_sums_kernel(int nf, const double *__restrict__ a,
       for (int k = 0; k < 5; k++) sh[t][k] += sh[t + s][k];
     __syncthreads();
   }
-  if (t == 0)
+  if (t == 0) {
     for (int k = 0; k <= m; k++) out[k] = sh[0][k];
+    if (grad)
+      for (int k = 0; k < m; k++) grad[k] += sh[0][1 + k];
+  }
 }
 
 struct VolArgs {
@@ -232,7 +236,8 @@ struct VolArgs {
 __global__ void adj_vertex_kernel(int nv, const int *__restrict__ vf_start,
                                   const int *__restrict__ vf_list, const double *__restrict__ corner,
                                   const double *__restrict__ fn, const double *__restrict__ dn,
-                                  const double *__restrict__ sums, VolArgs va, int tangent,
+                                  const double *__restrict__ sums,
+                                  const double *__restrict__ sums_t, VolArgs va, int tangent,
                                   double *__restrict__ out) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nv) return;
@@ -249,9 +254,9 @@ __global__ void adj_vertex_kernel(int nv, const int *__restrict__ vf_start,
     const double coef = va.on ? va.kV * (sums[0] - va.V0) / va.V0 : 0.0;
     for (int k = 0; k < 3; k++) out[3 * v + k] = f[k] - coef * g[k];
   } else {
-    // sums[0] = V (value pass), sums[1] = grad V . t (derivative pass)
+    // sums[0] = V (value pass), sums_t[0] = grad V . t (derivative pass)
     const double coef = va.on ? va.kV * (sums[0] - va.V0) / va.V0 : 0.0;
-    const double coef2 = va.on ? va.kV / va.V0 * sums[1] : 0.0;
+    const double coef2 = va.on ? va.kV / va.V0 * sums_t[0] : 0.0;
     for (int k = 0; k < 3; k++) out[3 * v + k] += f[k] - coef * dg[k] - coef2 * g[k];
   }
 }
@@ -281,21 +286,31 @@ __device__ __forceinline__ double dpeskin(double r) {
   return 0.0;
 }
 
-// Stencil of position p: base node floor(p) - 1 per axis, 1D weights w and their derivatives
-// dw with respect to p (= -d peskin(x - p)/dx).
+// Stencil of a vertex position: base node floor(p) - 1 per axis, the 1D weights w and their
+// derivatives dw with respect to p (= -d peskin(x - p)/dx). Computed once per vertex and
+// reverse step, then read by the three per-vertex passes (double square roots are costly
+// here: FP64 runs at 1/64 of the FP32 rate).
 struct Stencil {
   int base[3];
+  int pad;
   double w[3][4], dw[3][4];
 };
-__device__ __forceinline__ void stencil_of(const double p[3], Stencil &s) {
+
+__global__ void adj_stencil_kernel(int nv, const double *__restrict__ q, Stencil *__restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  Stencil s;
+  s.pad = 0;
   for (int k = 0; k < 3; k++) {
-    s.base[k] = (int)floor(p[k]) - 1;
+    const double p = q[3 * v + k];
+    s.base[k] = (int)floor(p) - 1;
     for (int d = 0; d < 4; d++) {
-      const double r = (double)(s.base[k] + d) - p[k];
+      const double r = (double)(s.base[k] + d) - p;
       s.w[k][d] = peskin(r);
       s.dw[k][d] = -dpeskin(r);
     }
   }
+  out[v] = s;
 }
 
 // z kind of a node: 0 fluid, 1 bottom wall, 2 top wall, -1 beyond the array (reading R9).
@@ -325,13 +340,16 @@ __device__ __forceinline__ size_t pull_source(int x, int y, int z, int i, const 
   return (size_t)i * L.ncell + node_of(x - cx(i), y - cy(i), sz, L);
 }
 
-// Post-streaming populations (deviations) at fluid node (x, y, z) from post-collision P.
-__device__ __forceinline__ void pull_dev(const double *__restrict__ P, int x, int y, int z,
+// Post-streaming populations (deviations, in double) at fluid node (x, y, z) from the
+// post-collision populations P as stored (double, or float for FP32 contexts).
+template <typename T>
+__device__ __forceinline__ void pull_dev(const T *__restrict__ P, int x, int y, int z,
                                          const LatArgs &L, double f[Q]) {
+#pragma unroll
   for (int i = 0; i < Q; i++) {
     bool bb;
     const size_t s = pull_source(x, y, z, i, L, bb);
-    f[i] = P[s] + (bb ? (cz(i) > 0 ? L.wb[i] : L.wt[i]) : 0.0);
+    f[i] = (double)P[s] + (bb ? (cz(i) > 0 ? L.wb[i] : L.wt[i]) : 0.0);
   }
 }
 
@@ -339,146 +357,216 @@ __device__ __forceinline__ void pull_dev(const double *__restrict__ P, int x, in
 __device__ __forceinline__ double velocity(const double f[Q], const double Ft[3], double rho0,
                                            double u[3]) {
   double drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
   for (int i = 0; i < Q; i++) {
     drho += f[i];
-    j[0] += cx(i) * f[i];
-    j[1] += cy(i) * f[i];
-    j[2] += cz(i) * f[i];
+    if (cx(i)) j[0] += cx(i) > 0 ? f[i] : -f[i];
+    if (cy(i)) j[1] += cy(i) > 0 ? f[i] : -f[i];
+    if (cz(i)) j[2] += cz(i) > 0 ? f[i] : -f[i];
   }
   const double rho = rho0 + drho;
-  for (int k = 0; k < 3; k++) u[k] = (j[k] + 0.5 * Ft[k]) / rho;
+  const double ir = 1.0 / rho;
+  for (int k = 0; k < 3; k++) u[k] = (j[k] + 0.5 * Ft[k]) * ir;
   return rho;
 }
 
-// Dense spreading of the forces at positions q onto the fluid nodes (F zeroed before).
-__global__ void adj_spread_kernel(int nv, const double *__restrict__ q,
+// Velocity and density after streaming at a node.
+struct alignas(32) NodeU {
+  double x, y, z, rho;
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// The per-vertex passes run one warp per vertex: lane l handles the stencil nodes
+// (dx, dy, dz) = (l & 3, (l >> 2) & 3, (l >> 4) + 2 h) for h = 0, 1.
+
+// Spreading at q_n onto the fluid nodes (Eq. 13): F += W phi. F is zero on entry at every
+// stencil node: the spreading transpose of the previous reverse step cleared it.
+__global__ void adj_spread_kernel(int nv, const Stencil *__restrict__ st,
                                   const double *__restrict__ phi, LatArgs L,
                                   double *__restrict__ F) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (v >= nv) return;
-  const double p[3] = {q[3 * v], q[3 * v + 1], q[3 * v + 2]};
-  Stencil s;
-  stencil_of(p, s);
-  for (int dz = 0; dz < 4; dz++) {
+  const Stencil &s = st[v];
+  const double ph[3] = {phi[3 * v], phi[3 * v + 1], phi[3 * v + 2]};
+  const int dx = lane & 3, dy = (lane >> 2) & 3;
+  for (int h = 0; h < 2; h++) {
+    const int dz = (lane >> 4) + 2 * h;
     const int z = s.base[2] + dz;
     if (zkind(z, L) != 0) continue;  // wall layer: force dropped; beyond: skipped
-    for (int dy = 0; dy < 4; dy++)
-      for (int dx = 0; dx < 4; dx++) {
-        const double w = s.w[0][dx] * s.w[1][dy] * s.w[2][dz];
-        const size_t n = node_of(s.base[0] + dx, s.base[1] + dy, z, L);
-        for (int k = 0; k < 3; k++) atomicAdd(&F[3 * n + k], w * phi[3 * v + k]);
-      }
+    const double w = s.w[0][dx] * s.w[1][dy] * s.w[2][dz];
+    const size_t n = node_of(s.base[0] + dx, s.base[1] + dy, z, L);
+    for (int k = 0; k < 3; k++) atomicAdd(&F[3 * n + k], w * ph[k]);
   }
 }
 
-// Interpolation^T: lam_qn_v = lam_v + sum_x (u(x) . lam_v) dW/dq_v, and lam_u(x) += W lam_v on
-// the fluid nodes, with u(x) the velocity of the step (wall velocity on the wall layers).
-__global__ void adj_interp_kernel(int nv, const double *__restrict__ q,
-                                  const double *__restrict__ lam, const double *__restrict__ Pn1,
-                                  const double *__restrict__ F, LatArgs L,
-                                  double *__restrict__ lam_qn, double *__restrict__ lam_u) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+// Velocity and density after streaming at every fluid node, U = (u, rho), from the
+// post-collision populations P_{n+1} and the step's total force g + F.
+template <typename T>
+__global__ void adj_moments_kernel(const T *__restrict__ P, const double *__restrict__ F,
+                                   LatArgs L, NodeU *__restrict__ U) {
+  const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (n >= L.ncell) return;
+  const int x = (int)(n % L.nx), y = (int)((n / L.nx) % L.ny), z = (int)(n / ((size_t)L.nx * L.ny));
+  if (zkind(z, L) != 0) return;
+  double f[Q], u[3];
+  pull_dev(P, x, y, z, L, f);
+  const double Ft[3] = {L.g[0] + F[3 * n], L.g[1] + F[3 * n + 1], L.g[2] + F[3 * n + 2]};
+  const double rho = velocity(f, Ft, L.rho0, u);
+  U[n] = NodeU{u[0], u[1], u[2], rho};
+}
+
+// Interpolation^T: lam_qn_v = lam_v + sum_x (u(x) . lam_v) dW/dq_v, and lam_u(x) += W lam_v
+// on the fluid nodes, with u(x) the velocity of the step (the wall velocity on wall layers).
+__global__ void adj_interp_t_kernel(int nv, const Stencil *__restrict__ st,
+                                    const double *__restrict__ lam, const NodeU *__restrict__ U,
+                                    LatArgs L, double *__restrict__ lam_qn,
+                                    double *__restrict__ lam_u) {
+  const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (v >= nv) return;
-  const double p[3] = {q[3 * v], q[3 * v + 1], q[3 * v + 2]};
+  const Stencil &s = st[v];
   const double l[3] = {lam[3 * v], lam[3 * v + 1], lam[3 * v + 2]};
-  Stencil s;
-  stencil_of(p, s);
+  const int dx = lane & 3, dy = (lane >> 2) & 3;
   double acc[3] = {0, 0, 0};
-  for (int dz = 0; dz < 4; dz++) {
+  for (int h = 0; h < 2; h++) {
+    const int dz = (lane >> 4) + 2 * h;
     const int z = s.base[2] + dz;
     const int kind = zkind(z, L);
     if (kind < 0) continue;
-    for (int dy = 0; dy < 4; dy++)
-      for (int dx = 0; dx < 4; dx++) {
-        const int x = s.base[0] + dx, y = s.base[1] + dy;
-        double u[3];
-        if (kind == 1) {
-          for (int k = 0; k < 3; k++) u[k] = L.ub[k];
-        } else if (kind == 2) {
-          for (int k = 0; k < 3; k++) u[k] = L.ut[k];
-        } else {
-          double f[Q];
-          pull_dev(Pn1, x, y, z, L, f);
-          const size_t n = node_of(x, y, z, L);
-          const double Ft[3] = {L.g[0] + F[3 * n], L.g[1] + F[3 * n + 1], L.g[2] + F[3 * n + 2]};
-          velocity(f, Ft, L.rho0, u);
-          const double w = s.w[0][dx] * s.w[1][dy] * s.w[2][dz];
-          for (int k = 0; k < 3; k++) atomicAdd(&lam_u[3 * n + k], w * l[k]);
-        }
-        const double ul = u[0] * l[0] + u[1] * l[1] + u[2] * l[2];
-        acc[0] += ul * s.dw[0][dx] * s.w[1][dy] * s.w[2][dz];
-        acc[1] += ul * s.w[0][dx] * s.dw[1][dy] * s.w[2][dz];
-        acc[2] += ul * s.w[0][dx] * s.w[1][dy] * s.dw[2][dz];
-      }
+    const double wx = s.w[0][dx], wy = s.w[1][dy], wz = s.w[2][dz];
+    double u[3];
+    if (kind == 1) {
+      for (int k = 0; k < 3; k++) u[k] = L.ub[k];
+    } else if (kind == 2) {
+      for (int k = 0; k < 3; k++) u[k] = L.ut[k];
+    } else {
+      const size_t n = node_of(s.base[0] + dx, s.base[1] + dy, z, L);
+      const NodeU un = U[n];
+      u[0] = un.x;
+      u[1] = un.y;
+      u[2] = un.z;
+      const double w = wx * wy * wz;
+      for (int k = 0; k < 3; k++) atomicAdd(&lam_u[3 * n + k], w * l[k]);
+    }
+    const double ul = u[0] * l[0] + u[1] * l[1] + u[2] * l[2];
+    acc[0] += ul * s.dw[0][dx] * wy * wz;
+    acc[1] += ul * wx * s.dw[1][dy] * wz;
+    acc[2] += ul * wx * wy * s.dw[2][dz];
   }
-  for (int k = 0; k < 3; k++) lam_qn[3 * v + k] = l[k] + acc[k];
+  for (int k = 0; k < 3; k++) acc[k] = warp_sum(acc[k]);
+  if (lane == 0)
+    for (int k = 0; k < 3; k++) lam_qn[3 * v + k] = l[k] + acc[k];
 }
 
-// Velocity moments^T at every fluid node with lam_u != 0: lam_F += lam_u/(2 rho), and the
-// adjoint of each pulled population, (c_i - u) . lam_u / rho, added to its source in lam_P.
-__global__ void adj_velocity_kernel(const double *__restrict__ lam_u,
-                                    const double *__restrict__ Pn1, const double *__restrict__ F,
-                                    LatArgs L, double *__restrict__ lam_F,
-                                    double *__restrict__ lam_P) {
+// Velocity moments^T at the fluid nodes with lam_u != 0: the adjoint of each pulled
+// population, (c_i - u) . lam_u / rho, added to its source in lam_P (its force part,
+// lam_u / (2 rho), is added by the collision transpose, which also clears lam_u).
+__global__ void adj_velocity_t_kernel(const double *__restrict__ lam_u,
+                                      const NodeU *__restrict__ U, LatArgs L,
+                                      double *__restrict__ lam_P) {
   const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (n >= L.ncell) return;
   const int x = (int)(n % L.nx), y = (int)((n / L.nx) % L.ny), z = (int)(n / ((size_t)L.nx * L.ny));
   if (zkind(z, L) != 0) return;
   const double lu[3] = {lam_u[3 * n], lam_u[3 * n + 1], lam_u[3 * n + 2]};
   if (lu[0] == 0.0 && lu[1] == 0.0 && lu[2] == 0.0) return;
-  double f[Q], u[3];
-  pull_dev(Pn1, x, y, z, L, f);
-  const double Ft[3] = {L.g[0] + F[3 * n], L.g[1] + F[3 * n + 1], L.g[2] + F[3 * n + 2]};
-  const double rho = velocity(f, Ft, L.rho0, u);
-  for (int k = 0; k < 3; k++) lam_F[3 * n + k] += lu[k] / (2.0 * rho);
+  const NodeU un = U[n];
+  const double ir = 1.0 / un.rho;
+  const double ulu = (un.x * lu[0] + un.y * lu[1] + un.z * lu[2]) * ir;
+  const double l[3] = {lu[0] * ir, lu[1] * ir, lu[2] * ir};
+#pragma unroll
   for (int i = 0; i < Q; i++) {
-    const double a = ((cx(i) - u[0]) * lu[0] + (cy(i) - u[1]) * lu[1] + (cz(i) - u[2]) * lu[2]) / rho;
+    double a = -ulu;
+    if (cx(i)) a += cx(i) > 0 ? l[0] : -l[0];
+    if (cy(i)) a += cy(i) > 0 ? l[1] : -l[1];
+    if (cz(i)) a += cz(i) > 0 ? l[2] : -l[2];
     bool bb;
     lam_P[pull_source(x, y, z, i, L, bb)] += a;  // each (source, direction) has one puller
   }
 }
 
-// Collision^T and streaming^T at every fluid node: mu = lam_P1(node), the adjoint of the
-// post-collision populations; writes the adjoint of the pulled pre-collision populations to
-// their sources in lam_P0 and adds the force part to lam_F.
-__global__ void adj_collide_kernel(const double *__restrict__ lam_P1, const double *__restrict__ Pn,
-                                   const double *__restrict__ F, LatArgs L, int fresh,
-                                   double *__restrict__ lam_P0, double *__restrict__ lam_F) {
+// Collision^T and streaming^T at every fluid node. mu = lam_P1 at the node is the adjoint of
+// the post-collision populations out_i = f_i - omega (f_i - feq_i(rho, u)) + S_i(u, F) of the
+// pulled pre-collision f (BGK with Guo forcing). With the moments of mu,
+//   m0 = sum w_i mu_i, m1 = sum w_i mu_i c_i, M2 = sum w_i mu_i c_i c_i^T,
+// the vector-Jacobian product is
+//   lam_f_j = (1 - omega) mu_j + A + B . (c_j - u) / rho,
+//   A = omega (m0 + 3 u.m1 + 4.5 u.M2 u - 1.5 u.u m0)                      (d/d rho)
+//   B = omega rho (3 m1 + 9 M2 u - 3 m0 u) + gamma (9 M2 Ft - 3 m0 Ft)     (d/d u)
+//   lam_F = B / (2 rho) + gamma (3 m1 - 3 m0 u + 9 M2 u)                     (d/d F)
+// (u depends on f through (sum c f + Ft/2)/rho; Ft = g + F). lam_f_j goes to the source of
+// the pulled population (a permutation: written once). The velocity-moment transpose of step
+// n+1 adds lam_u / (2 rho_{n+1}) to lam_F here, and lam_u is cleared for the next step.
+template <typename T>
+__global__ void adj_collide_t_kernel(const double *__restrict__ lam_P1, const T *__restrict__ Pn,
+                                     const double *__restrict__ F, const NodeU *__restrict__ U1,
+                                     double *__restrict__ lam_u, LatArgs L, int fresh,
+                                     double *__restrict__ lam_P0, double *__restrict__ lam_F) {
   const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (n >= L.ncell) return;
   const int x = (int)(n % L.nx), y = (int)((n / L.nx) % L.ny), z = (int)(n / ((size_t)L.nx * L.ny));
   if (zkind(z, L) != 0) return;
   double f[Q], mu[Q], u[3];
   if (fresh) {
-    for (int i = 0; i < Q; i++) f[i] = Pn[(size_t)i * L.ncell + n];
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = (double)Pn[(size_t)i * L.ncell + n];
   } else {
     pull_dev(Pn, x, y, z, L, f);
   }
+#pragma unroll
   for (int i = 0; i < Q; i++) mu[i] = lam_P1[(size_t)i * L.ncell + n];
   const double Ft[3] = {L.g[0] + F[3 * n], L.g[1] + F[3 * n + 1], L.g[2] + F[3 * n + 2]};
   const double rho = velocity(f, Ft, L.rho0, u);
-  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  double A = 0.0, B[3] = {0, 0, 0}, G[3] = {0, 0, 0};
+  const double ir = 1.0 / rho;
+  // moments of mu (c components are 0 or +-1: only additions)
+  double m0 = 0, m1[3] = {0, 0, 0}, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+#pragma unroll
   for (int i = 0; i < Q; i++) {
-    const double c[3] = {(double)cx(i), (double)cy(i), (double)cz(i)};
-    const double w = wgt(i);
-    const double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
-    const double cF = c[0] * Ft[0] + c[1] * Ft[1] + c[2] * Ft[2];
-    const double Qi = 3.0 * cu + 4.5 * cu * cu - 1.5 * uu;
-    A += mu[i] * w * (1.0 + Qi);
+    const double wm = wgt(i) * mu[i];
+    m0 += wm;
+    if (cx(i)) { m1[0] += cx(i) > 0 ? wm : -wm; mxx += wm; }
+    if (cy(i)) { m1[1] += cy(i) > 0 ? wm : -wm; myy += wm; }
+    if (cz(i)) { m1[2] += cz(i) > 0 ? wm : -wm; mzz += wm; }
+    if (cx(i) && cy(i)) mxy += cx(i) * cy(i) > 0 ? wm : -wm;
+    if (cx(i) && cz(i)) mxz += cx(i) * cz(i) > 0 ? wm : -wm;
+    if (cy(i) && cz(i)) myz += cy(i) * cz(i) > 0 ? wm : -wm;
+  }
+  const double M2u[3] = {mxx * u[0] + mxy * u[1] + mxz * u[2], mxy * u[0] + myy * u[1] + myz * u[2],
+                         mxz * u[0] + myz * u[1] + mzz * u[2]};
+  const double M2F[3] = {mxx * Ft[0] + mxy * Ft[1] + mxz * Ft[2],
+                         mxy * Ft[0] + myy * Ft[1] + myz * Ft[2],
+                         mxz * Ft[0] + myz * Ft[1] + mzz * Ft[2]};
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double um1 = u[0] * m1[0] + u[1] * m1[1] + u[2] * m1[2];
+  const double uM2u = u[0] * M2u[0] + u[1] * M2u[1] + u[2] * M2u[2];
+  const double A = L.omega * (m0 + 3.0 * um1 + 4.5 * uM2u - 1.5 * uu * m0);
+  double B[3], lf[3];
+  for (int k = 0; k < 3; k++) {
+    B[k] = L.omega * rho * (3.0 * m1[k] + 9.0 * M2u[k] - 3.0 * m0 * u[k]) +
+           L.gamma * (9.0 * M2F[k] - 3.0 * m0 * Ft[k]);
+    lf[k] = 0.5 * B[k] * ir + L.gamma * (3.0 * m1[k] - 3.0 * m0 * u[k] + 9.0 * M2u[k]);
+  }
+  const double lu[3] = {lam_u[3 * n], lam_u[3 * n + 1], lam_u[3 * n + 2]};
+  if (lu[0] != 0.0 || lu[1] != 0.0 || lu[2] != 0.0) {
+    const double h = 0.5 / U1[n].rho;
     for (int k = 0; k < 3; k++) {
-      // d out_i / d u = omega w rho (3 c + 9 (c.u) c - 3 u) + w gamma (9 (c.F) c - 3 F)
-      B[k] += mu[i] * (L.omega * w * rho * (3.0 * c[k] + 9.0 * cu * c[k] - 3.0 * u[k]) +
-                       w * L.gamma * (9.0 * cF * c[k] - 3.0 * Ft[k]));
-      // explicit d S_i / d F = w gamma (3 (c - u) + 9 (c.u) c)
-      G[k] += mu[i] * w * L.gamma * (3.0 * (c[k] - u[k]) + 9.0 * cu * c[k]);
+      lf[k] += lu[k] * h;
+      lam_u[3 * n + k] = 0.0;
     }
   }
-  A *= L.omega;
-  for (int k = 0; k < 3; k++) lam_F[3 * n + k] += B[k] / (2.0 * rho) + G[k];
+  for (int k = 0; k < 3; k++) lam_F[3 * n + k] = lf[k];
+  const double b[3] = {B[0] * ir, B[1] * ir, B[2] * ir};
+  const double s0 = A - (u[0] * b[0] + u[1] * b[1] + u[2] * b[2]);
+  const double om1 = 1.0 - L.omega;
+#pragma unroll
   for (int i = 0; i < Q; i++) {
-    const double du = ((cx(i) - u[0]) * B[0] + (cy(i) - u[1]) * B[1] + (cz(i) - u[2]) * B[2]) / rho;
-    const double lam = (1.0 - L.omega) * mu[i] + A + du;
+    double lam = om1 * mu[i] + s0;
+    if (cx(i)) lam += cx(i) > 0 ? b[0] : -b[0];
+    if (cy(i)) lam += cy(i) > 0 ? b[1] : -b[1];
+    if (cz(i)) lam += cz(i) > 0 ? b[2] : -b[2];
     if (fresh) {
       lam_P0[(size_t)i * L.ncell + n] = lam;
     } else {
@@ -489,76 +577,75 @@ __global__ void adj_collide_kernel(const double *__restrict__ lam_P1, const doub
 }
 
 // Spreading^T: lam_phi_v = sum_x W lam_F(x) over the fluid nodes, and
-// lam_qn_v += sum_x (phi_v . lam_F(x)) dW/dq_v.
-__global__ void adj_spread_t_kernel(int nv, const double *__restrict__ q,
+// lam_qn_v += sum_x (phi_v . lam_F(x)) dW/dq_v. The step's force field F is no longer
+// needed afterwards: its stencil nodes are cleared here, which leaves F zero for the next
+// reverse step's spreading.
+__global__ void adj_spread_t_kernel(int nv, const Stencil *__restrict__ st,
                                     const double *__restrict__ phi, const double *__restrict__ lam_F,
                                     LatArgs L, double *__restrict__ lam_phi,
-                                    double *__restrict__ lam_qn) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+                                    double *__restrict__ lam_qn, double *__restrict__ F) {
+  const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (v >= nv) return;
-  const double p[3] = {q[3 * v], q[3 * v + 1], q[3 * v + 2]};
+  const Stencil &s = st[v];
   const double ph[3] = {phi[3 * v], phi[3 * v + 1], phi[3 * v + 2]};
-  Stencil s;
-  stencil_of(p, s);
+  const int dx = lane & 3, dy = (lane >> 2) & 3;
   double lp[3] = {0, 0, 0}, acc[3] = {0, 0, 0};
-  for (int dz = 0; dz < 4; dz++) {
+  for (int h = 0; h < 2; h++) {
+    const int dz = (lane >> 4) + 2 * h;
     const int z = s.base[2] + dz;
     if (zkind(z, L) != 0) continue;
-    for (int dy = 0; dy < 4; dy++)
-      for (int dx = 0; dx < 4; dx++) {
-        const size_t n = node_of(s.base[0] + dx, s.base[1] + dy, z, L);
-        const double lf[3] = {lam_F[3 * n], lam_F[3 * n + 1], lam_F[3 * n + 2]};
-        const double w = s.w[0][dx] * s.w[1][dy] * s.w[2][dz];
-        for (int k = 0; k < 3; k++) lp[k] += w * lf[k];
-        const double pl = ph[0] * lf[0] + ph[1] * lf[1] + ph[2] * lf[2];
-        acc[0] += pl * s.dw[0][dx] * s.w[1][dy] * s.w[2][dz];
-        acc[1] += pl * s.w[0][dx] * s.dw[1][dy] * s.w[2][dz];
-        acc[2] += pl * s.w[0][dx] * s.w[1][dy] * s.dw[2][dz];
-      }
+    const size_t n = node_of(s.base[0] + dx, s.base[1] + dy, z, L);
+    const double lf[3] = {lam_F[3 * n], lam_F[3 * n + 1], lam_F[3 * n + 2]};
+    const double wx = s.w[0][dx], wy = s.w[1][dy], wz = s.w[2][dz];
+    const double w = wx * wy * wz;
+    for (int k = 0; k < 3; k++) {
+      lp[k] += w * lf[k];
+      F[3 * n + k] = 0.0;
+    }
+    const double pl = ph[0] * lf[0] + ph[1] * lf[1] + ph[2] * lf[2];
+    acc[0] += pl * s.dw[0][dx] * wy * wz;
+    acc[1] += pl * wx * s.dw[1][dy] * wz;
+    acc[2] += pl * wx * wy * s.dw[2][dz];
   }
   for (int k = 0; k < 3; k++) {
-    lam_phi[3 * v + k] = lp[k];
-    lam_qn[3 * v + k] += acc[k];
+    lp[k] = warp_sum(lp[k]);
+    acc[k] = warp_sum(acc[k]);
   }
-}
-
-__global__ void adj_accumulate_kernel(const double *__restrict__ sums, double *__restrict__ grad) {
-  if (threadIdx.x < 4) grad[threadIdx.x] += sums[1 + threadIdx.x];
+  if (lane == 0)
+    for (int k = 0; k < 3; k++) {
+      lam_phi[3 * v + k] = lp[k];
+      lam_qn[3 * v + k] += acc[k];
+    }
 }
 
 // --- host side ---------------------------------------------------------------------------
-
-// FP32 populations widened to double.
-__global__ void widen_kernel(const float *__restrict__ in, double *__restrict__ out, size_t n) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
-       k += (size_t)gridDim.x * blockDim.x)
-    out[k] = (double)in[k];
-}
 
 struct Adjoint {
   int nsteps = 0, every = 0, first_fresh = 0;
   std::vector<void *> ck_P;           // populations at steps 0, K, 2K, ..., nsteps (storage type)
   std::vector<double *> ck_q;         // positions at the same steps
-  std::vector<double *> seg_P, seg_q; // states of the segment being reversed
+  std::vector<void *> seg_P;          // states of the segment being reversed (storage type)
+  std::vector<double *> seg_q;
   double *lam_P[2] = {nullptr, nullptr};
   double *lam_q = nullptr, *lam_qn = nullptr, *lam_phi = nullptr, *lam_F = nullptr,
          *lam_u = nullptr, *F = nullptr, *phi = nullptr;
   double *fc = nullptr, *fn = nullptr, *fV = nullptr, *fj = nullptr, *dn = nullptr,
          *fdot = nullptr, *fpar = nullptr, *sums = nullptr, *sums_t = nullptr, *grad = nullptr;
+  NodeU *U = nullptr;       // [ncell] velocity and density after streaming of the step
+  Stencil *st = nullptr;    // [nv] stencils of the step's positions
 };
 
 void free_all(Adjoint *a) {
-  auto f = [](double *p) {
+  auto f = [](void *p) {
     if (p) cudaFree(p);
   };
-  for (void *p : a->ck_P)
-    if (p) cudaFree(p);
+  for (void *p : a->ck_P) f(p);
   for (double *p : a->ck_q) f(p);
-  for (double *p : a->seg_P) f(p);
+  for (void *p : a->seg_P) f(p);
   for (double *p : a->seg_q) f(p);
   f(a->lam_P[0]); f(a->lam_P[1]); f(a->lam_q); f(a->lam_qn); f(a->lam_phi); f(a->lam_F);
   f(a->lam_u); f(a->F); f(a->phi); f(a->fc); f(a->fn); f(a->fV); f(a->fj); f(a->dn); f(a->fdot);
-  f(a->fpar); f(a->sums); f(a->sums_t); f(a->grad);
+  f(a->fpar); f(a->sums); f(a->sums_t); f(a->grad); f(a->U); f(a->st);
   delete a;
 }
 
@@ -628,22 +715,7 @@ int snapshot_raw(Ctx &c, void *P, double *q) {
   return 0;
 }
 
-// A state of the segment being reversed, in double whatever the storage: the reverse step
-// linearises the double-precision step about it (for FP32 storage, about the FP32 trajectory).
-int snapshot(Ctx &c, double *P, double *q) {
-  const size_t n = (size_t)Q * c.ncell;
-  if (c.pop_size == sizeof(double)) {
-    ADJ_TRY(c, cudaMemcpyAsync(P, c.f[c.cur], n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-  } else {
-    widen_kernel<<<c.sm_count * 8, 256, 0, c.stream>>>((const float *)c.f[c.cur], P, n);
-    ADJ_TRY(c, cudaGetLastError());
-  }
-  ADJ_TRY(c, cudaMemcpyAsync(q, c.q, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToDevice,
-                             c.stream));
-  return 0;
-}
-
-// n steps with the health check of iblb_step
+// n steps queued with the health check of iblb_step at their end
 int run_steps(Ctx &c, int n) {
   ADJ_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
   if (int rc = enqueue_steps(c, n)) return rc;
@@ -653,39 +725,55 @@ int run_steps(Ctx &c, int n) {
   return health_status(c, hw);
 }
 
+// Recompute a segment: from the restored state, `len` steps, the state after each one copied
+// (as stored) to seg_P[m], seg_q[m]; everything queued, one health check at the end.
+int recompute_segment(Ctx &c, Adjoint *a, int len) {
+  ADJ_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
+  if (int rc = snapshot_raw(c, a->seg_P[0], a->seg_q[0])) return rc;
+  for (int m = 1; m <= len; m++) {
+    if (int rc = enqueue_steps(c, 1)) return rc;
+    if (int rc = snapshot_raw(c, a->seg_P[m], a->seg_q[m])) return rc;
+  }
+  int hw = 0;
+  ADJ_TRY(c, cudaMemcpyAsync(&hw, c.counters + 3, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  ADJ_TRY(c, cudaStreamSynchronize(c.stream));
+  return health_status(c, hw);
+}
+
 // Reverse step n: a->lam_q (of q_{n+1}) and a->lam_P[1] (of P_{n+1}) become those of q_n, P_n
-// in a->lam_qn and a->lam_P[0] (swapped by the caller).
-int reverse_step(Ctx &c, Adjoint *a, const double *Pn, const double *qn, const double *Pn1,
-                 int fresh) {
+// in a->lam_qn and a->lam_P[0] (swapped by the caller). Pn, Pn1 are stored populations (T).
+// No scratch field needs clearing: F and lam_u are zero between steps (cleared by their last
+// readers), lam_F and lam_P0 are overwritten at every fluid node.
+template <typename T>
+int reverse_step(Ctx &c, Adjoint *a, const T *Pn, const double *qn, const T *Pn1, int fresh) {
   const FaceArgs FA = face_args(c);
   const LatArgs L = lat_args(c);
   const VolArgs va{c.iface.volume_force_on, c.iface.kV, c.V0};
   const int tb = 128;
   const unsigned gf = (unsigned)((c.nf + tb - 1) / tb), gv = (unsigned)((c.nv + tb - 1) / tb);
+  const unsigned gw = (unsigned)((32L * c.nv + tb - 1) / tb);  // a warp per vertex
   const unsigned gn = (unsigned)((c.ncell + 255) / 256);
   cudaStream_t st = c.stream;
-  // forward pieces at q_n: forces, volume, dense force field
+  // forward pieces at q_n: forces, volume, stencils, the spread force field, the moments
   adj_face_value_kernel<<<gf, tb, 0, st>>>(FA, qn, a->fc, a->fn, a->fV);
-  adj_face_sums_kernel<<<1, 256, 0, st>>>(c.nf, a->fV, nullptr, 0, a->sums);
+  adj_face_sums_kernel<<<1, 256, 0, st>>>(c.nf, a->fV, nullptr, 0, a->sums, nullptr);
   adj_vertex_kernel<<<gv, tb, 0, st>>>(c.nv, c.vf_start, c.vf_list, a->fc, a->fn, nullptr, a->sums,
-                                       va, 0, a->phi);
-  ADJ_TRY(c, cudaMemsetAsync(a->F, 0, 3 * c.ncell * sizeof(double), st));
-  adj_spread_kernel<<<gv, tb, 0, st>>>(c.nv, qn, a->phi, L, a->F);
+                                       nullptr, va, 0, a->phi);
+  adj_stencil_kernel<<<gv, tb, 0, st>>>(c.nv, qn, a->st);
+  adj_spread_kernel<<<gw, tb, 0, st>>>(c.nv, a->st, a->phi, L, a->F);
+  adj_moments_kernel<T><<<gn, 256, 0, st>>>(Pn1, a->F, L, a->U);
   // interpolation^T, velocity^T, collision^T and streaming^T, spreading^T
-  ADJ_TRY(c, cudaMemsetAsync(a->lam_u, 0, 3 * c.ncell * sizeof(double), st));
-  adj_interp_kernel<<<gv, tb, 0, st>>>(c.nv, qn, a->lam_q, Pn1, a->F, L, a->lam_qn, a->lam_u);
-  ADJ_TRY(c, cudaMemsetAsync(a->lam_F, 0, 3 * c.ncell * sizeof(double), st));
-  adj_velocity_kernel<<<gn, 256, 0, st>>>(a->lam_u, Pn1, a->F, L, a->lam_F, a->lam_P[1]);
-  adj_collide_kernel<<<gn, 256, 0, st>>>(a->lam_P[1], Pn, a->F, L, fresh, a->lam_P[0], a->lam_F);
-  adj_spread_t_kernel<<<gv, tb, 0, st>>>(c.nv, qn, a->phi, a->lam_F, L, a->lam_phi, a->lam_qn);
-  // force Jacobian^T along lam_phi, and the parameter derivatives
+  adj_interp_t_kernel<<<gw, tb, 0, st>>>(c.nv, a->st, a->lam_q, a->U, L, a->lam_qn, a->lam_u);
+  adj_velocity_t_kernel<<<gn, 256, 0, st>>>(a->lam_u, a->U, L, a->lam_P[1]);
+  adj_collide_t_kernel<T><<<gn, 256, 0, st>>>(a->lam_P[1], Pn, a->F, a->U, a->lam_u, L, fresh,
+                                              a->lam_P[0], a->lam_F);
+  adj_spread_t_kernel<<<gw, tb, 0, st>>>(c.nv, a->st, a->phi, a->lam_F, L, a->lam_phi, a->lam_qn,
+                                         a->F);
+  // force Jacobian^T along lam_phi, and the parameter derivatives (added to grad)
   adj_face_tangent_kernel<<<gf, tb, 0, st>>>(FA, qn, a->lam_phi, a->fj, a->dn, a->fdot, a->fpar);
-  adj_face_sums_kernel<<<1, 256, 0, st>>>(c.nf, a->fdot, a->fpar, 4, a->sums_t);
-  // sums: [V]; sums_t: [grad V . lam_phi, 4 parameter dots]; the vertex pass wants (V, gV.t)
-  ADJ_TRY(c, cudaMemcpyAsync(a->sums + 1, a->sums_t, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  adj_face_sums_kernel<<<1, 256, 0, st>>>(c.nf, a->fdot, a->fpar, 4, a->sums_t, a->grad);
   adj_vertex_kernel<<<gv, tb, 0, st>>>(c.nv, c.vf_start, c.vf_list, a->fj, a->fn, a->dn, a->sums,
-                                       va, 1, a->lam_qn);
-  adj_accumulate_kernel<<<1, 32, 0, st>>>(a->sums_t, a->grad);
+                                       a->sums_t, va, 1, a->lam_qn);
   ADJ_TRY(c, cudaGetLastError());
   return 0;
 }
@@ -766,9 +854,12 @@ int iblb_adjoint_gradient(iblb_ctx *h, const double *dJdq, double *dJdtheta) {
     ADJ_TRY(c, iblb::dmalloc(&a->sums, 8));
     ADJ_TRY(c, iblb::dmalloc(&a->sums_t, 8));
     ADJ_TRY(c, iblb::dmalloc(&a->grad, 4));
+    ADJ_TRY(c, cudaMalloc((void **)&a->U, c.ncell * sizeof(iblb::NodeU)));
+    ADJ_TRY(c, cudaMalloc((void **)&a->st, (size_t)c.nv * sizeof(iblb::Stencil)));
     for (int m = 0; m <= a->every; m++) {
-      double *P = nullptr, *q = nullptr;
-      ADJ_TRY(c, iblb::dmalloc(&P, pn));
+      void *P = nullptr;
+      double *q = nullptr;
+      ADJ_TRY(c, cudaMalloc(&P, pn * c.pop_size));
       a->seg_P.push_back(P);
       ADJ_TRY(c, iblb::dmalloc(&q, qn));
       a->seg_q.push_back(q);
@@ -777,6 +868,9 @@ int iblb_adjoint_gradient(iblb_ctx *h, const double *dJdq, double *dJdtheta) {
   ADJ_TRY(c, cudaMemcpyAsync(a->lam_q, dJdq, qn * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   ADJ_TRY(c, cudaMemsetAsync(a->lam_P[0], 0, pn * sizeof(double), c.stream));
   ADJ_TRY(c, cudaMemsetAsync(a->lam_P[1], 0, pn * sizeof(double), c.stream));
+  // zero between reverse steps (each step leaves them so)
+  ADJ_TRY(c, cudaMemsetAsync(a->F, 0, 3 * c.ncell * sizeof(double), c.stream));
+  ADJ_TRY(c, cudaMemsetAsync(a->lam_u, 0, 3 * c.ncell * sizeof(double), c.stream));
   ADJ_TRY(c, cudaMemsetAsync(a->grad, 0, 4 * sizeof(double), c.stream));
   const int nseg = (int)a->ck_P.size() - 1;
   int rc = 0;
@@ -785,14 +879,15 @@ int iblb_adjoint_gradient(iblb_ctx *h, const double *dJdq, double *dJdtheta) {
     const int len = (a->nsteps - first) < a->every ? a->nsteps - first : a->every;
     const int fresh0 = s == 0 ? a->first_fresh : 0;
     rc = iblb::restore_state(c, a->ck_P[s], a->ck_q[s], fresh0);
-    if (rc == 0) rc = iblb::snapshot(c, a->seg_P[0], a->seg_q[0]);
-    for (int m = 1; m <= len && rc == 0; m++) {
-      rc = iblb::run_steps(c, 1);
-      if (rc == 0) rc = iblb::snapshot(c, a->seg_P[m], a->seg_q[m]);
-    }
+    if (rc == 0) rc = iblb::recompute_segment(c, a, len);
     for (int m = len - 1; m >= 0 && rc == 0; m--) {
-      rc = iblb::reverse_step(c, a, a->seg_P[m], a->seg_q[m], a->seg_P[m + 1],
-                              s == 0 && m == 0 && a->first_fresh);
+      const int fresh = s == 0 && m == 0 && a->first_fresh;
+      if (c.pop_size == sizeof(double))
+        rc = iblb::reverse_step<double>(c, a, (const double *)a->seg_P[m], a->seg_q[m],
+                                        (const double *)a->seg_P[m + 1], fresh);
+      else
+        rc = iblb::reverse_step<float>(c, a, (const float *)a->seg_P[m], a->seg_q[m],
+                                       (const float *)a->seg_P[m + 1], fresh);
       std::swap(a->lam_q, a->lam_qn);
       std::swap(a->lam_P[0], a->lam_P[1]);
     }
