@@ -183,8 +183,10 @@ int iblb_profile(iblb_ctx *ctx, double *k1_ms, int64_t *k1_launches, int64_t *ke
    Nothing is allocated: the only scratch is a 32 KB array of per-block partial sums that the
    library holds on every device that loads it, until the process exits. Callers in a host
    framework that owns all device memory, or in a loop that must not pay for cudaMalloc's
-   device-wide synchronisation, can use it. The first call on each device looks up that
-   array's device address, so make the first call before any stream capture begins.
+   device-wide synchronisation, can use it. Every call looks up that array's device address in
+   the caller's current context (so the call stays correct under a non-primary context and
+   after cudaDeviceReset); the first call on a device also loads the library's device code into
+   that context, so make the first call before any stream capture begins.
    Limits and errors: nf <= 1,048,576 (IBLB_ECAPACITY beyond), nf >= 1 and non-NULL pointers
    (IBLB_EINVAL otherwise), IBLB_ECUDA if a launch fails. Every call shares the one array and
    overwrites the partials it uses, so calls that overlap on the GPU (on different streams)

@@ -9,38 +9,29 @@
 //
 // The array is a file-scope __device__ variable, so every GPU that loads this library keeps
 // its 32 KB until the process exits. Host code may not pass the variable's name to a kernel:
-// in host code that name is a host-side stand-in, not a device address. The device address
-// is looked up with cudaGetSymbolAddress by the first call on each device, with that device
-// current, and cached; make that first call before any stream capture begins.
-#include <mutex>
-
+// in host code that name is a host-side stand-in, not a device address. Every call looks the
+// device address up with cudaGetSymbolAddress, with the caller's device and context current,
+// and passes it to the kernels. Looking it up per call (a host-side table lookup once the
+// module is loaded) keeps it right when the caller runs under a context other than the
+// device's primary one, or after cudaDeviceReset, where an address saved from an earlier
+// call would belong to a context that no longer holds it. The first call on a device loads
+// this file's device code into the current context: make it before any stream capture.
 #include "iblb_internal.cuh"
 
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kMaxPartials = 4096;  // => at most 4096 * 256 = 1,048,576 faces
+constexpr int kMaxPartials = 4096;
+constexpr long long kMaxFaces = (long long)kMaxPartials * kBlock;  // 1,048,576 faces
 
 static __device__ __align__(256) double g_volume_partials[kMaxPartials];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double *g_partials_ptr[kMaxDevices] = {};
-
-// Device address of g_volume_partials on the current device (looked up on first use).
-cudaError_t partials_on_current_device(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+// Device address of g_volume_partials in the current context.
+cudaError_t partials_in_current_context(double **out) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_volume_partials);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_partials_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_volume_partials);
-    if (e != cudaSuccess) return e;
-    g_partials_ptr[dev] = static_cast<double *>(p);
-  }
-  *out = g_partials_ptr[dev];
+  *out = static_cast<double *>(p);
   return cudaSuccess;
 }
 
@@ -90,10 +81,10 @@ extern "C" int iblb_mesh_volume_noalloc(const double *q_dev, const int32_t *face
                                         int32_t nf, const double *centre, double *V_dev,
                                         void *cuda_stream) {
   if (!q_dev || !faces_dev || !centre || !V_dev || nf < 1) return IBLB_EINVAL;
+  if ((long long)nf > kMaxFaces) return IBLB_ECAPACITY;  // before any arithmetic on nf
   const int blocks = (nf + kBlock - 1) / kBlock;
-  if (blocks > kMaxPartials) return IBLB_ECAPACITY;
   double *partials = nullptr;
-  if (partials_on_current_device(&partials) != cudaSuccess) return IBLB_ECUDA;
+  if (partials_in_current_context(&partials) != cudaSuccess) return IBLB_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   face_volume_partials_kernel<<<blocks, kBlock, 0, s>>>(nf, q_dev, faces_dev, centre[0],
                                                         centre[1], centre[2], partials);

@@ -66,5 +66,7 @@ def test_noalloc_volume_rejects_bad_sizes_before_launching():
     c = np.zeros(3)
     dummy = 1  # never dereferenced: the size checks come first
     assert binding.mesh_volume_noalloc(dummy, dummy, 4096 * 256 + 1, c, dummy) == binding.IBLB_ECAPACITY
+    # the size test comes before the block count is formed, which would overflow int32 here
+    assert binding.mesh_volume_noalloc(dummy, dummy, 2**31 - 1, c, dummy) == binding.IBLB_ECAPACITY
     assert binding.mesh_volume_noalloc(dummy, dummy, 0, c, dummy) == binding.IBLB_EINVAL
     assert L.iblb_mesh_volume_noalloc(None, None, 10, None, None, None) == binding.IBLB_EINVAL
