@@ -170,3 +170,42 @@ def test_full_ensemble_sampled_instances():
         ref = _alone(wls[k], "fp32", [5])
         _same(b.contexts[k], ref)
     b.close()
+
+
+def _oracle_ensemble():
+    """One instance per pre-stressed model class of Table I, uneven edges, walls on."""
+    a = 0.01
+    return [
+        inputs.scaled_wetting(24, 20, 2, 4.5, alpha=(a, 0, 0), eps=0.5 * a),            # droplet
+        inputs.scaled_shear(20, 2, 4.0, alpha=(a, 0, a)),                                # softly coated
+        inputs.scaled_wetting(28, 22, 3, 5.5, alpha=(a, a, a), eps=0.8 * a),            # rigidly coated
+    ]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_matches_the_oracle(precision):
+    """The batched path against the FP64 oracle itself (not only against the library stepped
+    one context at a time): 120 steps of three instances of different sizes and classes, at
+    the FP32 bars (u and rho relative L2 <= 1e-5, vertices <= 1e-6 R; FP64 to rounding)."""
+    import oracle
+    from paper_2305_18919_gb300 import binding
+    from pairs import rel_l2
+    wls = _oracle_ensemble()
+    for wl in wls:
+        wl.centre = (wl.centre[0] - 0.37, wl.centre[1] + 0.21, wl.centre[2])
+    b = binding.Batch.from_workloads(wls, precision=precision)
+    b.step(120)
+    assert list(b.status()) == [0, 0, 0]
+    for lat, wl in zip(b.contexts, wls):
+        ref = oracle.Simulation.from_workload(wl)
+        ref.step(120)
+        r0, u0 = ref.fields()
+        r1, u1 = lat.fields()
+        dq = np.abs(lat.vertices() - ref.vertices()).max()
+        if precision == "fp32":
+            assert rel_l2(u1, u0) < 1e-5 and rel_l2(r1 - 1, r0 - 1) < 1e-5
+            assert dq < 1e-6 * wl.radius
+        else:
+            assert rel_l2(u1, u0) < 1e-11 and dq < 1e-11 * wl.radius
+        ref.close()
+    b.close()
