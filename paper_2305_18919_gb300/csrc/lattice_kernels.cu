@@ -984,63 +984,135 @@ __global__ void __launch_bounds__(128) stream_collide_kernel_multi(
   }
 }
 
-// K1t: stream-collide of the fluid nodes of the active tiles with body + interface force,
-// one warp per tile (grid-stride), each thread the node pair (x0, x0 + 1) of a tile row as in
-// K1. Runs after K1 of the same step and overwrites those nodes. Pairs whose interface force
-// is zero keep K1's result, which is already the post-collision state with the body force
-// alone.
+// K1t: the fluid nodes of the active tiles with body + interface force. Runs after K1 of the
+// same step and corrects K1's result there in place. The collision (BGK with Guo forcing,
+// Eqs. 9-10) keeps rho and turns the momentum j into j + Ft (Ft the total force), so K1's
+// output f0 at a node (the collision with the body force g alone) gives rho = rho0 + sum f0
+// and u0 = (sum c f0 - g/2)/rho without the pre-collision populations; with the interface
+// force F the post-collision populations are f0 + D,
+//   D_i = omega (f^eq_i(rho, uF) - f^eq_i(rho, u0)) + S_i(uF, g + F) - S_i(u0, g),
+//   uF = u0 + F/(2 rho).
+// K1t therefore reads and writes only each node's own populations, no pulled neighbours.
+// A warp takes an x-pair of tiles (tx even, tx + 1) when both are active, else one tile;
+// each thread a node pair (x0, x0 + 1) of an 8-node row, idle where its tile is not active.
+// Node pairs whose interface force is zero keep K1's result, which is already final.
 template <typename real, typename S>
 struct TilesArgs {
-  const S *fin;
   S *fout;
-  const int *slot_tile, *nslots_ptr;
+  const int *slot_tile, *nslots_ptr, *tile_slot;
   const Vec4<real> *Fslot;
   LatParams<real> P;
   int max_slots;
 };
 
-template <typename real, typename S, bool FIRST>
+// f (deviations, after the collision with the body force g alone) becomes the collision
+// with g + F; see K1t above. Opposite directions are handled in symmetric/antisymmetric
+// pairs as in collide().
+template <typename real>
+__device__ __forceinline__ void force_correction(real f[Q], const real F[3],
+                                                 const LatParams<real> &P) {
+  real drho = f[0], Jx = 0, Jy = 0, Jz = 0;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    drho += f[i] + f[i + 1];
+    const real d = f[i] - f[i + 1];
+    if (cx(i)) Jx += cx(i) > 0 ? d : -d;
+    if (cy(i)) Jy += cy(i) > 0 ? d : -d;
+    if (cz(i)) Jz += cz(i) > 0 ? d : -d;
+  }
+  const real rho = P.rho0 + drho;
+  const real ir = real(1) / rho;
+  const real u0[3] = {(Jx - real(0.5) * P.g[0]) * ir, (Jy - real(0.5) * P.g[1]) * ir,
+                      (Jz - real(0.5) * P.g[2]) * ir};
+  const real dl[3] = {real(0.5) * F[0] * ir, real(0.5) * F[1] * ir, real(0.5) * F[2] * ir};
+  const real uF[3] = {u0[0] + dl[0], u0[1] + dl[1], u0[2] + dl[2]};
+  const real sm[3] = {uF[0] + u0[0], uF[1] + u0[1], uF[2] + u0[2]};
+  const real Ft[3] = {P.g[0] + F[0], P.g[1] + F[1], P.g[2] + F[2]};
+  const real orho = P.omega * rho;
+  const real gm = P.guo;
+  // the direction-independent part: -1.5 omega rho (uF^2 - u0^2) - 3 gamma (uF.Ft - u0.g)
+  const real q0 = real(-1.5) * orho * (dl[0] * sm[0] + dl[1] * sm[1] + dl[2] * sm[2]) -
+                  real(3) * gm *
+                      ((uF[0] * Ft[0] + uF[1] * Ft[1] + uF[2] * Ft[2]) -
+                       (u0[0] * P.g[0] + u0[1] * P.g[1] + u0[2] * P.g[2]));
+  f[0] += real(wgt(0)) * q0;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const real w = (real)wgt(i);
+    const real cd = cx(i) * dl[0] + cy(i) * dl[1] + cz(i) * dl[2];
+    const real cs = cx(i) * sm[0] + cy(i) * sm[1] + cz(i) * sm[2];
+    const real cuF = cx(i) * uF[0] + cy(i) * uF[1] + cz(i) * uF[2];
+    const real cu0 = cx(i) * u0[0] + cy(i) * u0[1] + cz(i) * u0[2];
+    const real cFt = cx(i) * Ft[0] + cy(i) * Ft[1] + cz(i) * Ft[2];
+    const real cg = cx(i) * P.g[0] + cy(i) * P.g[1] + cz(i) * P.g[2];
+    const real cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
+    const real sym = w * (real(4.5) * orho * cd * cs + real(9) * gm * (cFt * cuF - cg * cu0) + q0);
+    const real asym = w * real(3) * (orho * cd + gm * cF);
+    f[i] += sym + asym;
+    f[i + 1] += sym - asym;
+  }
+}
+
+template <typename real, typename S>
 __device__ __forceinline__ void tiles_body(const TilesArgs<real, S> &A, int bid, int nb) {
-  const S *__restrict__ fin = A.fin;
+  using V2 = typename Storage<S>::V2;
   S *__restrict__ fout = A.fout;
   const int *__restrict__ slot_tile = A.slot_tile;
+  const int *__restrict__ tile_slot = A.tile_slot;
   const Vec4<real> *__restrict__ Fslot = A.Fslot;
   const LatParams<real> P = A.P;  // held in registers: the loop below is latency-bound
   const int nslots = min(*A.nslots_ptr, A.max_slots);
   const int lane = threadIdx.x & 31;
-  const int px = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
-  const int cell = 16 * lz + 4 * ly + 2 * px;
+  const int xq = lane & 3, ly = (lane >> 2) & 3;  // node pair 2 xq, 2 xq + 1 of an 8-node row
+  const int half = xq >> 1;                         // 0: the even tile, 1: the odd tile
   const int warps = blockDim.x >> 5;
   for (int s = bid * warps + (threadIdx.x >> 5); s < nslots; s += nb * warps) {
-    const Vec4<real> Fa = Fslot[(size_t)s * TILE_CELLS + cell];
-    const Vec4<real> Fb = Fslot[(size_t)s * TILE_CELLS + cell + 1];
     const int t = slot_tile[s];
     const int tx = t % P.ntx, ty = (t / P.ntx) % P.nty, tz = t / (P.ntx * P.nty);
-    const int x0 = tx * TILE + 2 * px, y = ty * TILE + ly, z = tz * TILE + lz;
-    if (z >= P.nz || (P.has_walls && (z == 0 || z == P.nz - 1))) continue;
-    if (Fa.x == real(0) && Fa.y == real(0) && Fa.z == real(0) && Fb.x == real(0) &&
-        Fb.y == real(0) && Fb.z == real(0))
-      continue;
-    real a[Q], b[Q];
-    load_pair<real, S, FIRST>(fin, P, x0, y, z, a, b);
-    const real FA[3] = {P.g[0] + Fa.x, P.g[1] + Fa.y, P.g[2] + Fa.z};
-    const real FB[3] = {P.g[0] + Fb.x, P.g[1] + Fb.y, P.g[2] + Fb.z};
-    collide<real, true>(a, FA, P);
-    collide<real, true>(b, FB, P);
-    store_pair(fout, P, (size_t)z * P.nx * P.ny + (size_t)y * P.nx + x0, a, b);
+    const int px = tx ^ 1;
+    const int sp = px < P.ntx ? tile_slot[t - tx + px] : -1;
+    if (sp >= 0 && (tx & 1)) continue;  // an active pair is taken from its even tile
+    const int sl = (tx & 1) ? -1 : s, sr = (tx & 1) ? s : sp;
+    const int ss = half ? sr : sl;
+    if (ss < 0) continue;  // this half of the pair is not active
+    const int x0 = (tx & ~1) * TILE + 2 * xq, y = ty * TILE + ly;
+    for (int h = 0; h < 2; h++) {
+      const int lz = (lane >> 4) + 2 * h;
+      const int z = tz * TILE + lz;
+      if (z >= P.nz || (P.has_walls && (z == 0 || z == P.nz - 1))) continue;
+      const int cell = 16 * lz + 4 * ly + 2 * (xq & 1);
+      const Vec4<real> Fa = Fslot[(size_t)ss * TILE_CELLS + cell];
+      const Vec4<real> Fb = Fslot[(size_t)ss * TILE_CELLS + cell + 1];
+      if (Fa.x == real(0) && Fa.y == real(0) && Fa.z == real(0) && Fb.x == real(0) &&
+          Fb.y == real(0) && Fb.z == real(0))
+        continue;
+      const size_t n = (size_t)z * P.nx * P.ny + (size_t)y * P.nx + x0;
+      real a[Q], b[Q];
+#pragma unroll
+      for (int i = 0; i < Q; i++) {
+        widen2(*reinterpret_cast<const V2 *>(fout + (size_t)i * P.ncell + n), a[i], b[i]);
+        a[i] *= real(kinv<S>(i));
+        b[i] *= real(kinv<S>(i));
+      }
+      const real FA[3] = {Fa.x, Fa.y, Fa.z};
+      const real FB[3] = {Fb.x, Fb.y, Fb.z};
+      force_correction<real>(a, FA, P);
+      force_correction<real>(b, FB, P);
+      store_pair(fout, P, n, a, b);
+    }
   }
 }
 
-template <typename real, typename S, bool FIRST>
+template <typename real, typename S>
 __global__ void __launch_bounds__(128) stream_collide_tiles_kernel(const TilesArgs<real, S> A) {
-  tiles_body<real, S, FIRST>(A, blockIdx.x, gridDim.x);
+  tiles_body<real, S>(A, blockIdx.x, gridDim.x);
 }
 
 template <typename real, typename S>
 __global__ void __launch_bounds__(128) stream_collide_tiles_kernel_multi(
     const TilesArgs<real, S> *__restrict__ all, const int *__restrict__ start, int n) {
   const MultiBlock m = multi_block(start, n);
-  tiles_body<real, S, false>(all[m.inst], m.block, m.nblocks);
+  tiles_body<real, S>(all[m.inst], m.block, m.nblocks);
 }
 
 // K1b: velocity after streaming at every node of the active interface tiles.
@@ -1352,10 +1424,10 @@ cudaError_t stream_collide_t(Ctx &c, int first, cudaStream_t st) {
 template <typename real, typename S>
 TilesArgs<real, S> tiles_args(const Ctx &c) {
   TilesArgs<real, S> a;
-  a.fin = (const S *)c.f[c.cur];
   a.fout = (S *)c.f[c.cur ^ 1];
   a.slot_tile = c.slot_tile[c.map];
   a.nslots_ptr = c.counters + c.map;
+  a.tile_slot = c.tile_slot[c.map];
   a.Fslot = (const Vec4<real> *)c.Fslot[c.map];
   a.P = lat_params<real>(c);
   a.max_slots = c.max_slots;
@@ -1409,10 +1481,8 @@ StreamArgs<real, S> stream_args(const Ctx &c) {
 template <typename real, typename S>
 cudaError_t stream_collide_tiles_t(Ctx &c, int first, cudaStream_t st) {
   const int grid = tiles_blocks(c, false);
-  if (first)
-    stream_collide_tiles_kernel<real, S, true><<<grid, 128, 0, st>>>(tiles_args<real, S>(c));
-  else
-    stream_collide_tiles_kernel<real, S, false><<<grid, 128, 0, st>>>(tiles_args<real, S>(c));
+  (void)first;  // K1t corrects K1's output in place, whatever K1 read
+  stream_collide_tiles_kernel<real, S><<<grid, 128, 0, st>>>(tiles_args<real, S>(c));
   return cudaGetLastError();
 }
 
