@@ -199,29 +199,35 @@ __global__ void adj_face_tangent_kernel(FaceArgs A, const double *__restrict__ q
   }
 }
 
-// Fixed-order sums over faces (one block): out[0] = sum a, out[1..m] = sums of b's columns;
-// with grad, the b sums (the parameter derivatives of the step) are also added to grad[0..m-1].
-__global__ void adj_face_sums_kernel(int nf, const double *__restrict__ a,
-                                     const double *__restrict__ b, int m,
-                                     double *__restrict__ out, double *__restrict__ grad) {
-  __shared__ double sh[256][5];
-  const int t = threadIdx.x;
+// Fixed-order sums over faces (one block of 1024 threads): out[0] = sum a, out[1..m] = sums of
+// b's columns; with grad, the b sums (the parameter derivatives of the step) are also added to
+// grad[0..m-1]. Strided per-thread sums, then warp shuffles, then one warp over the warps.
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads) adj_face_sums_kernel(
+    int nf, const double *__restrict__ a, const double *__restrict__ b, int m,
+    double *__restrict__ out, double *__restrict__ grad) {
+  __shared__ double sh[kSumThreads / 32][5];
+  const int t = threadIdx.x, lane = t & 31, wq = t >> 5;
   double acc[5] = {0, 0, 0, 0, 0};
-  for (int j = t; j < nf; j += 256) {
+  for (int j = t; j < nf; j += kSumThreads) {
     acc[0] += a[j];
     for (int k = 0; k < m; k++) acc[1 + k] += b[(size_t)m * j + k];
   }
-  for (int k = 0; k < 5; k++) sh[t][k] = acc[k];
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (t < s)
-      for (int k = 0; k < 5; k++) sh[t][k] += sh[t + s][k];
-    __syncthreads();
+  for (int k = 0; k <= m; k++) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wq][k] = v;
   }
-  if (t == 0) {
-    for (int k = 0; k <= m; k++) out[k] = sh[0][k];
-    if (grad)
-      for (int k = 0; k < m; k++) grad[k] += sh[0][1 + k];
+  __syncthreads();
+  if (wq == 0) {
+    for (int k = 0; k <= m; k++) {
+      double v = sh[lane][k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        out[k] = v;
+        if (grad && k > 0) grad[k - 1] += v;
+      }
+    }
   }
 }
 
@@ -272,45 +278,49 @@ struct LatArgs {
   double wb[19], wt[19];      // moving-wall terms of the bounce-back (deviation units)
 };
 
-__device__ __forceinline__ double peskin(double r) {
-  const double a = fabs(r);
-  if (a <= 1.0) return 0.125 * (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a));
-  if (a <= 2.0) return 0.125 * (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a));
-  return 0.0;
-}
-// d peskin / d r
-__device__ __forceinline__ double dpeskin(double r) {
-  const double a = fabs(r), s = r < 0 ? -1.0 : 1.0;
-  if (a <= 1.0) return s * 0.125 * (-2.0 + (2.0 - 4.0 * a) / sqrt(1.0 + 4.0 * a - 4.0 * a * a));
-  if (a <= 2.0) return s * 0.125 * (-2.0 - (6.0 - 4.0 * a) / sqrt(-7.0 + 12.0 * a - 4.0 * a * a));
-  return 0.0;
+// Peskin's 4-point function (Eq. 15, reading R2) and its derivative, sharing the root.
+__device__ __forceinline__ void peskin_wdw(double r, double &w, double &dwdr) {
+  const double a = fabs(r), sg = r < 0 ? -1.0 : 1.0;
+  if (a <= 1.0) {
+    const double s = sqrt(1.0 + 4.0 * a - 4.0 * a * a);
+    w = 0.125 * (3.0 - 2.0 * a + s);
+    dwdr = sg * 0.125 * (-2.0 + (2.0 - 4.0 * a) / s);
+  } else if (a <= 2.0) {
+    const double s = sqrt(-7.0 + 12.0 * a - 4.0 * a * a);
+    w = 0.125 * (5.0 - 2.0 * a - s);
+    dwdr = sg * 0.125 * (-2.0 - (6.0 - 4.0 * a) / s);
+  } else {
+    w = 0.0;
+    dwdr = 0.0;
+  }
 }
 
 // Stencil of a vertex position: base node floor(p) - 1 per axis, the 1D weights w and their
 // derivatives dw with respect to p (= -d peskin(x - p)/dx). Computed once per vertex and
-// reverse step, then read by the three per-vertex passes (double square roots are costly
-// here: FP64 runs at 1/64 of the FP32 rate).
+// reverse step, then read by the three per-vertex passes (double square roots and divisions
+// are costly here: FP64 runs at 1/64 of the FP32 rate).
 struct Stencil {
   int base[3];
   int pad;
   double w[3][4], dw[3][4];
 };
 
+// one thread per (vertex, axis)
 __global__ void adj_stencil_kernel(int nv, const double *__restrict__ q, Stencil *__restrict__ out) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nv) return;
-  Stencil s;
-  s.pad = 0;
-  for (int k = 0; k < 3; k++) {
-    const double p = q[3 * v + k];
-    s.base[k] = (int)floor(p) - 1;
-    for (int d = 0; d < 4; d++) {
-      const double r = (double)(s.base[k] + d) - p;
-      s.w[k][d] = peskin(r);
-      s.dw[k][d] = -dpeskin(r);
-    }
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * nv) return;
+  const int v = t / 3, k = t - 3 * v;
+  const double p = q[t];
+  const int base = (int)floor(p) - 1;
+  Stencil &s = out[v];
+  s.base[k] = base;
+  if (k == 0) s.pad = 0;
+  for (int d = 0; d < 4; d++) {
+    double w, dwdr;
+    peskin_wdw((double)(base + d) - p, w, dwdr);
+    s.w[k][d] = w;
+    s.dw[k][d] = -dwdr;
   }
-  out[v] = s;
 }
 
 // z kind of a node: 0 fluid, 1 bottom wall, 2 top wall, -1 beyond the array (reading R9).
@@ -340,33 +350,38 @@ __device__ __forceinline__ size_t pull_source(int x, int y, int z, int i, const 
   return (size_t)i * L.ncell + node_of(x - cx(i), y - cy(i), sz, L);
 }
 
-// Post-streaming populations (deviations, in double) at fluid node (x, y, z) from the
-// post-collision populations P as stored (double, or float for FP32 contexts).
-template <typename T>
+// Post-streaming populations (deviations) at fluid node (x, y, z) from the post-collision
+// populations P as stored, in the arithmetic type A of the forward state: double for FP64
+// contexts; float for FP32 contexts, whose forward step ran in float (the reverse pass
+// linearises the double-precision step about that trajectory; its rho and u are formed in
+// float, like the forward step's, and the adjoint arithmetic itself stays double).
+template <typename A, typename T>
 __device__ __forceinline__ void pull_dev(const T *__restrict__ P, int x, int y, int z,
-                                         const LatArgs &L, double f[Q]) {
+                                         const LatArgs &L, A f[Q]) {
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     bool bb;
     const size_t s = pull_source(x, y, z, i, L, bb);
-    f[i] = (double)P[s] + (bb ? (cz(i) > 0 ? L.wb[i] : L.wt[i]) : 0.0);
+    f[i] = (A)P[s] + (bb ? (A)(cz(i) > 0 ? L.wb[i] : L.wt[i]) : A(0));
   }
 }
 
-// Velocity (Guo shift with the total force g + F) of deviations f; returns rho.
-__device__ __forceinline__ double velocity(const double f[Q], const double Ft[3], double rho0,
-                                           double u[3]) {
-  double drho = 0, j[3] = {0, 0, 0};
+// Velocity (Guo shift with the total force g + F) of deviations f; returns rho. Opposite
+// directions are summed in pairs.
+template <typename A>
+__device__ __forceinline__ A velocity(const A f[Q], const A Ft[3], A rho0, A u[3]) {
+  A drho = f[0], j[3] = {0, 0, 0};
 #pragma unroll
-  for (int i = 0; i < Q; i++) {
-    drho += f[i];
-    if (cx(i)) j[0] += cx(i) > 0 ? f[i] : -f[i];
-    if (cy(i)) j[1] += cy(i) > 0 ? f[i] : -f[i];
-    if (cz(i)) j[2] += cz(i) > 0 ? f[i] : -f[i];
+  for (int i = 1; i < Q; i += 2) {
+    drho += f[i] + f[i + 1];
+    const A d = f[i] - f[i + 1];
+    if (cx(i)) j[0] += cx(i) > 0 ? d : -d;
+    if (cy(i)) j[1] += cy(i) > 0 ? d : -d;
+    if (cz(i)) j[2] += cz(i) > 0 ? d : -d;
   }
-  const double rho = rho0 + drho;
-  const double ir = 1.0 / rho;
-  for (int k = 0; k < 3; k++) u[k] = (j[k] + 0.5 * Ft[k]) * ir;
+  const A rho = rho0 + drho;
+  const A ir = A(1) / rho;
+  for (int k = 0; k < 3; k++) u[k] = (j[k] + A(0.5) * Ft[k]) * ir;
   return rho;
 }
 
@@ -412,11 +427,12 @@ __global__ void adj_moments_kernel(const T *__restrict__ P, const double *__rest
   if (n >= L.ncell) return;
   const int x = (int)(n % L.nx), y = (int)((n / L.nx) % L.ny), z = (int)(n / ((size_t)L.nx * L.ny));
   if (zkind(z, L) != 0) return;
-  double f[Q], u[3];
-  pull_dev(P, x, y, z, L, f);
-  const double Ft[3] = {L.g[0] + F[3 * n], L.g[1] + F[3 * n + 1], L.g[2] + F[3 * n + 2]};
-  const double rho = velocity(f, Ft, L.rho0, u);
-  U[n] = NodeU{u[0], u[1], u[2], rho};
+  using A = T;  // the forward state's arithmetic type
+  A f[Q], u[3];
+  pull_dev<A>(P, x, y, z, L, f);
+  const A Ft[3] = {(A)(L.g[0] + F[3 * n]), (A)(L.g[1] + F[3 * n + 1]), (A)(L.g[2] + F[3 * n + 2])};
+  const A rho = velocity<A>(f, Ft, (A)L.rho0, u);
+  U[n] = NodeU{(double)u[0], (double)u[1], (double)u[2], (double)rho};
 }
 
 // Interpolation^T: lam_qn_v = lam_v + sum_x (u(x) . lam_v) dW/dq_v, and lam_u(x) += W lam_v
@@ -509,30 +525,36 @@ __global__ void adj_collide_t_kernel(const double *__restrict__ lam_P1, const T 
   if (n >= L.ncell) return;
   const int x = (int)(n % L.nx), y = (int)((n / L.nx) % L.ny), z = (int)(n / ((size_t)L.nx * L.ny));
   if (zkind(z, L) != 0) return;
-  double f[Q], mu[Q], u[3];
+  using A = T;  // the forward state's arithmetic type
+  A f[Q], ua[3];
   if (fresh) {
 #pragma unroll
-    for (int i = 0; i < Q; i++) f[i] = (double)Pn[(size_t)i * L.ncell + n];
+    for (int i = 0; i < Q; i++) f[i] = (A)Pn[(size_t)i * L.ncell + n];
   } else {
-    pull_dev(Pn, x, y, z, L, f);
+    pull_dev<A>(Pn, x, y, z, L, f);
   }
+  const double Ft[3] = {L.g[0] + F[3 * n], L.g[1] + F[3 * n + 1], L.g[2] + F[3 * n + 2]};
+  const A Fta[3] = {(A)Ft[0], (A)Ft[1], (A)Ft[2]};
+  const double rho = (double)velocity<A>(f, Fta, (A)L.rho0, ua);
+  const double u[3] = {(double)ua[0], (double)ua[1], (double)ua[2]};
+  const double ir = 1.0 / rho;
+  double mu[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) mu[i] = lam_P1[(size_t)i * L.ncell + n];
-  const double Ft[3] = {L.g[0] + F[3 * n], L.g[1] + F[3 * n + 1], L.g[2] + F[3 * n + 2]};
-  const double rho = velocity(f, Ft, L.rho0, u);
-  const double ir = 1.0 / rho;
-  // moments of mu (c components are 0 or +-1: only additions)
-  double m0 = 0, m1[3] = {0, 0, 0}, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+  // moments of mu from opposite pairs: c c^T is the same for both, c changes sign
+  double m0 = wgt(0) * mu[0], m1[3] = {0, 0, 0}, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0,
+         myz = 0;
 #pragma unroll
-  for (int i = 0; i < Q; i++) {
-    const double wm = wgt(i) * mu[i];
-    m0 += wm;
-    if (cx(i)) { m1[0] += cx(i) > 0 ? wm : -wm; mxx += wm; }
-    if (cy(i)) { m1[1] += cy(i) > 0 ? wm : -wm; myy += wm; }
-    if (cz(i)) { m1[2] += cz(i) > 0 ? wm : -wm; mzz += wm; }
-    if (cx(i) && cy(i)) mxy += cx(i) * cy(i) > 0 ? wm : -wm;
-    if (cx(i) && cz(i)) mxz += cx(i) * cz(i) > 0 ? wm : -wm;
-    if (cy(i) && cz(i)) myz += cy(i) * cz(i) > 0 ? wm : -wm;
+  for (int i = 1; i < Q; i += 2) {
+    const double ws = wgt(i) * (mu[i] + mu[i + 1]);
+    const double wd = wgt(i) * (mu[i] - mu[i + 1]);
+    m0 += ws;
+    if (cx(i)) { m1[0] += cx(i) > 0 ? wd : -wd; mxx += ws; }
+    if (cy(i)) { m1[1] += cy(i) > 0 ? wd : -wd; myy += ws; }
+    if (cz(i)) { m1[2] += cz(i) > 0 ? wd : -wd; mzz += ws; }
+    if (cx(i) && cy(i)) mxy += cx(i) * cy(i) > 0 ? ws : -ws;
+    if (cx(i) && cz(i)) mxz += cx(i) * cz(i) > 0 ? ws : -ws;
+    if (cy(i) && cz(i)) myz += cy(i) * cz(i) > 0 ? ws : -ws;
   }
   const double M2u[3] = {mxx * u[0] + mxy * u[1] + mxz * u[2], mxy * u[0] + myy * u[1] + myz * u[2],
                          mxz * u[0] + myz * u[1] + mzz * u[2]};
@@ -542,7 +564,7 @@ __global__ void adj_collide_t_kernel(const double *__restrict__ lam_P1, const T 
   const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const double um1 = u[0] * m1[0] + u[1] * m1[1] + u[2] * m1[2];
   const double uM2u = u[0] * M2u[0] + u[1] * M2u[1] + u[2] * M2u[2];
-  const double A = L.omega * (m0 + 3.0 * um1 + 4.5 * uM2u - 1.5 * uu * m0);
+  const double Arho = L.omega * (m0 + 3.0 * um1 + 4.5 * uM2u - 1.5 * uu * m0);
   double B[3], lf[3];
   for (int k = 0; k < 3; k++) {
     B[k] = L.omega * rho * (3.0 * m1[k] + 9.0 * M2u[k] - 3.0 * m0 * u[k]) +
@@ -559,19 +581,26 @@ __global__ void adj_collide_t_kernel(const double *__restrict__ lam_P1, const T 
   }
   for (int k = 0; k < 3; k++) lam_F[3 * n + k] = lf[k];
   const double b[3] = {B[0] * ir, B[1] * ir, B[2] * ir};
-  const double s0 = A - (u[0] * b[0] + u[1] * b[1] + u[2] * b[2]);
+  const double s0 = Arho - (u[0] * b[0] + u[1] * b[1] + u[2] * b[2]);
   const double om1 = 1.0 - L.omega;
+  double lam[Q];
+  lam[0] = om1 * mu[0] + s0;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {  // c.b changes sign between opposite directions
+    double cb = 0.0;
+    if (cx(i)) cb += cx(i) > 0 ? b[0] : -b[0];
+    if (cy(i)) cb += cy(i) > 0 ? b[1] : -b[1];
+    if (cz(i)) cb += cz(i) > 0 ? b[2] : -b[2];
+    lam[i] = om1 * mu[i] + s0 + cb;
+    lam[i + 1] = om1 * mu[i + 1] + s0 - cb;
+  }
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    double lam = om1 * mu[i] + s0;
-    if (cx(i)) lam += cx(i) > 0 ? b[0] : -b[0];
-    if (cy(i)) lam += cy(i) > 0 ? b[1] : -b[1];
-    if (cz(i)) lam += cz(i) > 0 ? b[2] : -b[2];
     if (fresh) {
-      lam_P0[(size_t)i * L.ncell + n] = lam;
+      lam_P0[(size_t)i * L.ncell + n] = lam[i];
     } else {
       bool bb;
-      lam_P0[pull_source(x, y, z, i, L, bb)] = lam;  // a permutation: written once
+      lam_P0[pull_source(x, y, z, i, L, bb)] = lam[i];  // a permutation: written once
     }
   }
 }
@@ -749,29 +778,32 @@ int reverse_step(Ctx &c, Adjoint *a, const T *Pn, const double *qn, const T *Pn1
   const FaceArgs FA = face_args(c);
   const LatArgs L = lat_args(c);
   const VolArgs va{c.iface.volume_force_on, c.iface.kV, c.V0};
-  const int tb = 128;
+  // small blocks for the per-face and per-vertex passes: a few thousand threads spread over
+  // all SMs (their double arithmetic, not memory, sets their time)
+  const int tb = 32, tw = 128;
   const unsigned gf = (unsigned)((c.nf + tb - 1) / tb), gv = (unsigned)((c.nv + tb - 1) / tb);
-  const unsigned gw = (unsigned)((32L * c.nv + tb - 1) / tb);  // a warp per vertex
+  const unsigned gs = (unsigned)((3 * c.nv + tb - 1) / tb);     // a thread per (vertex, axis)
+  const unsigned gw = (unsigned)((32L * c.nv + tw - 1) / tw);   // a warp per vertex
   const unsigned gn = (unsigned)((c.ncell + 255) / 256);
   cudaStream_t st = c.stream;
   // forward pieces at q_n: forces, volume, stencils, the spread force field, the moments
   adj_face_value_kernel<<<gf, tb, 0, st>>>(FA, qn, a->fc, a->fn, a->fV);
-  adj_face_sums_kernel<<<1, 256, 0, st>>>(c.nf, a->fV, nullptr, 0, a->sums, nullptr);
+  adj_face_sums_kernel<<<1, kSumThreads, 0, st>>>(c.nf, a->fV, nullptr, 0, a->sums, nullptr);
   adj_vertex_kernel<<<gv, tb, 0, st>>>(c.nv, c.vf_start, c.vf_list, a->fc, a->fn, nullptr, a->sums,
                                        nullptr, va, 0, a->phi);
-  adj_stencil_kernel<<<gv, tb, 0, st>>>(c.nv, qn, a->st);
-  adj_spread_kernel<<<gw, tb, 0, st>>>(c.nv, a->st, a->phi, L, a->F);
+  adj_stencil_kernel<<<gs, tb, 0, st>>>(c.nv, qn, a->st);
+  adj_spread_kernel<<<gw, tw, 0, st>>>(c.nv, a->st, a->phi, L, a->F);
   adj_moments_kernel<T><<<gn, 256, 0, st>>>(Pn1, a->F, L, a->U);
   // interpolation^T, velocity^T, collision^T and streaming^T, spreading^T
-  adj_interp_t_kernel<<<gw, tb, 0, st>>>(c.nv, a->st, a->lam_q, a->U, L, a->lam_qn, a->lam_u);
+  adj_interp_t_kernel<<<gw, tw, 0, st>>>(c.nv, a->st, a->lam_q, a->U, L, a->lam_qn, a->lam_u);
   adj_velocity_t_kernel<<<gn, 256, 0, st>>>(a->lam_u, a->U, L, a->lam_P[1]);
   adj_collide_t_kernel<T><<<gn, 256, 0, st>>>(a->lam_P[1], Pn, a->F, a->U, a->lam_u, L, fresh,
                                               a->lam_P[0], a->lam_F);
-  adj_spread_t_kernel<<<gw, tb, 0, st>>>(c.nv, a->st, a->phi, a->lam_F, L, a->lam_phi, a->lam_qn,
+  adj_spread_t_kernel<<<gw, tw, 0, st>>>(c.nv, a->st, a->phi, a->lam_F, L, a->lam_phi, a->lam_qn,
                                          a->F);
   // force Jacobian^T along lam_phi, and the parameter derivatives (added to grad)
   adj_face_tangent_kernel<<<gf, tb, 0, st>>>(FA, qn, a->lam_phi, a->fj, a->dn, a->fdot, a->fpar);
-  adj_face_sums_kernel<<<1, 256, 0, st>>>(c.nf, a->fdot, a->fpar, 4, a->sums_t, a->grad);
+  adj_face_sums_kernel<<<1, kSumThreads, 0, st>>>(c.nf, a->fdot, a->fpar, 4, a->sums_t, a->grad);
   adj_vertex_kernel<<<gv, tb, 0, st>>>(c.nv, c.vf_start, c.vf_list, a->fj, a->fn, a->dn, a->sums,
                                        a->sums_t, va, 1, a->lam_qn);
   ADJ_TRY(c, cudaGetLastError());
