@@ -110,9 +110,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(wl, seconds_target=20.0):
-    """The FP64 oracle, as it stands, on a bounded number of full steps of the same workload."""
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo; 'unknown' where it is not given)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                return line.split(":", 1)[1].strip()
+        for line in open("/proc/cpuinfo"):  # Arm: implementer / part numbers only
+            if line.lower().startswith("cpu part"):
+                return "Arm CPU part " + line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_mlups(wl, seconds_target, threads):
+    """The FP64 oracle, as it stands, on a bounded number of full steps of the workload with
+    `threads` threads (0: all host cores); returns (MLUPS, steps, seconds, threads, set-up s)."""
     import oracle
+    used = oracle.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
     t0 = time.perf_counter()
     sim = oracle.Simulation.from_workload(wl)
     setup = time.perf_counter() - t0
@@ -125,10 +142,21 @@ def cpu_baseline(wl, seconds_target=20.0):
         if el >= seconds_target or steps >= 1000:
             break
     sim.close()
-    mlups = wl.cells * steps / el / 1e6
-    return {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full IB-LB steps of the {wl.nx}x{wl.ny}x{wl.nz} workload "
-                      f"(FP64 oracle, single thread, {el:.1f} s timed, set-up {setup:.1f} s untimed)"}
+    return wl.cells * steps / el / 1e6, steps, el, used, setup
+
+
+def cpu_baseline(wl, seconds_target=20.0):
+    """The FP64 oracle on the host cores (its per-node loops split over z-planes by OpenMP),
+    with the single-thread figure beside it: bounded samples of full steps of the same
+    workload."""
+    v1, n1, e1, _, _ = _oracle_mlups(wl, seconds_target, 1)
+    vN, nN, eN, used, setup = _oracle_mlups(wl, seconds_target, 0)
+    return {"value": round(vN, 4), "unit": "MLUPS", "cores": used, "kind": "oracle",
+            "sample": f"{nN} full IB-LB steps of the {wl.nx}x{wl.ny}x{wl.nz} workload (FP64 "
+                      f"oracle, {used} threads, {eN:.1f} s timed, set-up {setup:.1f} s untimed)",
+            "single_thread": {"value": round(v1, 4), "unit": "MLUPS", "cores": 1,
+                              "sample": f"{n1} full steps, {e1:.1f} s timed"},
+            "host": {"nproc": os.cpu_count(), "cpu_model": cpu_model()}}
 
 
 def run_reference(args, wl, rank):
@@ -136,6 +164,7 @@ def run_reference(args, wl, rank):
     if rank != 0:
         return
     import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
     t0 = time.perf_counter()
     sim = oracle.Simulation.from_workload(wl)
     setup = time.perf_counter() - t0
@@ -157,10 +186,11 @@ def run_reference(args, wl, rank):
         "n_gpus": args.gpus, "steps": k, "warmup": warm + 1, "ms_per_step": round(el / k * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_of(wl),
-        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": f"{k} full IB-LB steps of the {wl.nx}x{wl.ny}x{wl.nz} workload "
-                                   f"timed of {args.steps} requested (FP64 oracle, single thread; "
-                                   f"set-up {setup:.1f} s untimed)"},
+                                   f"timed of {args.steps} requested (FP64 oracle, {cores} threads; "
+                                   f"set-up {setup:.1f} s untimed)",
+                         "host": {"nproc": os.cpu_count(), "cpu_model": cpu_model()}},
         "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -272,8 +302,22 @@ def time_variant(wl, precision, steps, warmup, sc=("auto", 0, 0, 0)):
             "ms_per_step": round(ms / steps, 5), "steps": steps, "bytes_per_cell": bpc,
             "k1_ms_avg": round(k1_avg, 5),
             "k1_frac": round(bpc * fluid / (k1_avg * 1e-3) / 1e9 / peak, 4),
+            "step_frac": round(bpc * fluid / (ms / steps * 1e-3) / 1e9 / peak, 4),
             "interface_sms": sms, "kernel": kernel,
             "traffic": int(round(per_node * fluid)) if per_node is not None else None}
+
+
+def time_workloads(steps, warmup):
+    """The two other single-box workloads, each in its own precision: the 32^3 shear box (FP64,
+    304 B per node) and the 128 x 128 x 96 static-wetting box (FP32, 152 B per node); same
+    timing as the headline, MLUPS and the roofline fractions of the stream-collide pass and of
+    the whole step."""
+    out = {}
+    for wl in (inputs.shear_32_fp64(), inputs.wetting_128x128x96()):
+        r = time_variant(wl, wl.precision, steps, warmup)
+        r["config"] = config_of(wl)
+        out[wl.name] = r
+    return out
 
 
 def time_ensemble(steps, warmup, n=96, seed=2305, ib_sms=0):
@@ -464,6 +508,8 @@ def run_gpu(args, wl, rank, world):
     }
     if variants:
         line["precision_variants"] = variants
+    if rank == 0 and world == 1 and args.workload_steps > 0 and wl.name.startswith("shear256"):
+        line["workloads"] = time_workloads(args.workload_steps, args.warmup)
     if rank == 0 and world == 1 and args.ensemble_steps > 0 and wl.name.startswith("shear256"):
         line["ensemble"] = time_ensemble(args.ensemble_steps, 10)
     if rank == 0 and world == 1 and args.adjoint_steps > 0 and wl.name.startswith("shear256"):
@@ -483,6 +529,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--adjoint-steps", type=int, default=5000,
                     help="steps of the 64^3 adjoint workload timed beside the headline (0: skip)")
+    ap.add_argument("--workload-steps", type=int, default=2000,
+                    help="steps timed for the 32^3 FP64 shear and 128x128x96 FP32 wetting "
+                         "workloads reported beside the headline (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=200,
                     help="steps timed for the 96-box batched ensemble reported beside the "
                          "headline (0: skip)")
