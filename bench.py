@@ -222,7 +222,8 @@ def k1_source_hash():
     return h.hexdigest()
 
 
-K1_PROFILES = ("stream_collide_kernel_shear256.md", "stream_collide_staged_kernel_shear256_fp16.md")
+K1_PROFILES = ("stream_collide_kernel_shear256.md", "stream_collide_staged_kernel_shear256_fp16.md",
+               "stream_collide_staged_kernel_shear256_bf16.md")
 
 
 def k1_traffic_per_node(kernel):
@@ -356,6 +357,10 @@ def time_ensemble(steps, warmup, n=96, seed=2305, ib_sms=0):
             "step_frac": round(152 * fluid / (ms / steps * 1e-3) / 1e9 / peak, 4),
             "sequential_value": round(replica_mlups(1, cells, steps, seq_s), 1),
             "k1_rows_chosen": {str(r): rows.count(r) for r in sorted(set(rows))},
+            "eps_over_alpha_range": [0.0, 0.1],
+            "eps_note": "wall strength eps/alpha_bar drawn uniformly in [0, 0.1] rather than the "
+                        "workload's [0, 1]: at the upper end the finest meshes are pulled "
+                        "through the wall within a few steps, in the FP64 oracle as well",
             "path": "iblb_batch_step: each kernel of a step one launch over all instances "
                     "(8 launches per step), FP32"}
 

@@ -1,8 +1,19 @@
-"""The shear observables on the GPU path against the paper's small-deformation theory (Sec. V):
-the rigidly coated particle of the 256^3 shear workload (alpha = abar (1, 1, 1), Ca = 0.051)
-reaches a steady deformation index near Eq. deformation. Measured on GB300: D = 0.045 against
-0.0374 (1.20x: this workload runs at Re = 2.5 with R/H = 0.16, where the paper's Re = 0.01
-theory is not exact) and Theta = 49.4 degrees, steady to 0.001 from step 9800 to 20000."""
+"""The shear observables on the GPU path against the paper's small-deformation theory (Sec. IV)
+and the Taylor deformation of the 16-bit storage forms against FP32 (the 256^3 shear workload:
+rigidly coated particle, alpha = abar (1, 1, 1), Ca = 0.051, Re = 2.5, 20000 steps).
+
+Measured on GB300 (FP32): the particle first deforms with the flow, D = 0.0196 at t = 0.039
+(in units of the inverse shear rate) against the affine t/2 = 0.0197 that Eq. evJK starts
+from; the lattice flow then overshoots (D = 0.099 at t = 0.35, an inertial transient that the
+Stokes-limit theory does not have) and settles at 0.045, 1.20 times the steady state of Eq.
+evJK (0.0373) and of Eq. deformation (0.0374); Theta 49.4 degrees (the workload runs at
+Re = 2.5 with R/H = 0.16, the theory at Re -> 0 in an unbounded fluid).
+
+16-bit storage against FP32 over the same run: FP16 (scaled by 1024/w_i, 11-bit significand)
+ends 2.6 % off in D and within 1.0 degree in Theta; BF16 (8-bit significand) 20.5 % and 5.9
+degrees: the interface force changes a population by about 3e-4 of its deviation from
+w_i rho0, below BF16's resolution, so much of it is rounded away every step.
+"""
 import math
 
 import numpy as np
@@ -11,26 +22,58 @@ import torch
 
 pytestmark = pytest.mark.gpu
 
+STEPS, SAMPLE = 20000, 250
 
-def test_coated_particle_deformation_near_theory():
+
+def _run(precision):
     from paper_2305_18919_gb300 import binding, inputs, observables as ob
     wl = inputs.shear_256_fp32()
-    lat = binding.Lattice.from_workload(wl, precision="fp32")
+    lat = binding.Lattice.from_workload(wl, precision=precision)
     nz, H = wl.nz, wl.nz - 2
     z = np.arange(nz)
     u = np.zeros((wl.nz, wl.ny, wl.nx, 3))
     u[..., 0] = (wl.wall_u_bottom[0] + (wl.wall_u_top[0] - wl.wall_u_bottom[0]) * (z - 0.5) / H)[:, None, None]
     lat.init_equilibrium(np.ones((wl.nz, wl.ny, wl.nx)), u)
     _, faces = wl.mesh()
-    lat.step(10000)
-    D1, _ = ob.deformation(torch.tensor(lat.vertices()), faces)
-    lat.step(2000)
-    D2, th = ob.deformation(torch.tensor(lat.vertices()), faces)
+    rows = []
+    for k in range(STEPS // SAMPLE):
+        lat.step(SAMPLE)
+        D, th = ob.deformation(torch.tensor(lat.vertices()), faces)
+        rows.append((float(D), float(th)))
     lat.close()
-    nu = (wl.tau - 0.5) / 3.0
+    return np.array(rows)
+
+
+@pytest.fixture(scope="module")
+def runs():
+    return {p: _run(p) for p in ("fp32", "fp16", "bf16")}
+
+
+def _theory():
+    from paper_2305_18919_gb300 import inputs, observables as ob
+    wl = inputs.shear_256_fp32()
+    H = wl.nz - 2
     gamma = (wl.wall_u_top[0] - wl.wall_u_bottom[0]) / H
-    Ca = nu * wl.radius * gamma / wl.alpha[0]
-    D_theory = ob.theory_deformation(wl.alpha, Ca)
-    assert abs(float(D2) - float(D1)) < 0.003                 # steady
-    assert 1.0 < float(D2) / D_theory < 1.4                   # near Eq. deformation
-    assert 40.0 < math.degrees(float(th)) < 55.0              # inclined near the extension axis
+    Ca = (wl.tau - 0.5) / 3.0 * wl.radius * gamma / wl.alpha[0]
+    t, D, th = ob.bbr_evolution(wl.alpha, Ca, STEPS * gamma, dt=1e-3, every=1)
+    return wl, gamma, Ca, t, D
+
+
+def test_coated_particle_against_the_small_deformation_theory(runs):
+    from paper_2305_18919_gb300 import observables as ob
+    wl, gamma, Ca, t, D_ode = _theory()
+    r = runs["fp32"]
+    t_first = SAMPLE * gamma
+    assert abs(r[0, 0] / (0.5 * t_first) - 1.0) < 0.1           # affine start, D = t/2
+    tail = r[-int(0.4 * len(r)):, 0]                              # the last 8000 steps
+    assert np.ptp(tail) < 0.003                                   # steady
+    assert 1.0 < tail[-1] / D_ode[-1] < 1.4                       # near Eq. evJK's steady state
+    assert abs(D_ode[-1] / ob.theory_deformation(wl.alpha, Ca) - 1.0) < 0.01
+    assert 40.0 < math.degrees(r[-1, 1]) < 55.0                   # inclined near the extension axis
+
+
+def test_16_bit_storage_deformation_against_fp32(runs):
+    d32, d16, dbf = runs["fp32"], runs["fp16"], runs["bf16"]
+    assert abs(d16[-1, 0] / d32[-1, 0] - 1.0) < 0.05
+    assert np.degrees(np.abs(d16[:, 1] - d32[:, 1]).max()) < 2.0
+    assert abs(dbf[-1, 0] / d32[-1, 0] - 1.0) < 0.3
