@@ -187,6 +187,19 @@ __device__ __forceinline__ void tile_force(const int *__restrict__ tile_slot,
   }
 }
 
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+
+// n / (hi + lo) for |lo| << |hi| and r1 ~ 1/hi: q0 = n r1, then the residual
+// n - q0 hi - q0 lo (the first product exactly, by a fused multiply-add) corrects it once.
+template <typename real>
+__device__ __forceinline__ real quotient(real n, real hi, real lo, real r1) {
+  const real q0 = n * r1;
+  real e = fma_(-q0, hi, n);
+  e = fma_(-q0, lo, e);
+  return fma_(e, r1, q0);
+}
+
 // BGK collision with Guo forcing (Eqs. 9-10) of one node's shifted populations f, storing
 // the post-collision populations at node n of fout. Opposite directions i, i+1 (i odd) share
 // c.u and c.F up to sign, so each pair is computed from its symmetric and antisymmetric parts:
@@ -205,21 +218,25 @@ __device__ __forceinline__ void collide(real f[Q], const real F[3], const LatPar
     if (cy(i)) jy += cy(i) > 0 ? d : -d;
     if (cz(i)) jz += cz(i) > 0 ? d : -d;
   }
-  // rho = rho0 + drho is never rounded as a whole: 1/rho carries the rounding remainder of
+  // rho = rho0 + drho is never rounded as a whole: rho_lo carries the rounding remainder of
   // the sum (Fast2Sum, |rho0| >= |drho|), and rho X is expanded as rho0 X + drho X
   const real rho_hi = P.rho0 + drho;
   const real rho_lo = (P.rho0 - rho_hi) + drho;
   const real r1 = real(1) / rho_hi;
-  const real inv_rho = r1 * (real(1) - rho_lo * r1);
   real ux = jx, uy = jy, uz = jz;
   if (FORCE) {
     ux += real(0.5) * F[0];
     uy += real(0.5) * F[1];
     uz += real(0.5) * F[2];
   }
-  ux *= inv_rho;
-  uy *= inv_rho;
-  uz *= inv_rho;
+  // u = j'/(rho_hi + rho_lo): a first quotient and one residual correction by fused
+  // multiply-adds, which keeps u within about an ulp of the exact quotient. The float
+  // rounding of u is what the FP32 path's drift from the FP64 solution grows from (the other
+  // roundings of the collision, the storage and the interface part matter two to three
+  // orders of magnitude less), so it is worth the six extra multiply-adds.
+  ux = quotient(ux, rho_hi, rho_lo, r1);
+  uy = quotient(uy, rho_hi, rho_lo, r1);
+  uz = quotient(uz, rho_hi, rho_lo, r1);
   const real uu15 = real(1.5) * (ux * ux + uy * uy + uz * uz);
   const real om = P.omega;
   real uF3 = 0;
@@ -955,8 +972,16 @@ struct StreamArgs {
   int force;    // the body force is non-zero
 };
 
+// Blocks per SM the batched pass is compiled for: 6 (80 registers) for FP32, where it keeps
+// the occupancy it has without the velocity correction (93 registers otherwise); no bound for
+// the others, which would spill under it.
 template <typename real, typename S>
-__global__ void __launch_bounds__(128) stream_collide_kernel_multi(
+struct MultiMinBlocks {
+  static constexpr int value = sizeof(real) == 4 && sizeof(S) == 4 ? 6 : 1;
+};
+
+template <typename real, typename S>
+__global__ void __launch_bounds__(128, MultiMinBlocks<real, S>::value) stream_collide_kernel_multi(
     const StreamArgs<real, S> *__restrict__ all, const int *__restrict__ start, int n) {
   const MultiBlock m = multi_block(start, n);
   const StreamArgs<real, S> &A = all[m.inst];

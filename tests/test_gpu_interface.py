@@ -99,32 +99,21 @@ def test_shear32_fp64_1000_steps():
     assert np.abs(gpu.vertices() - ref.vertices()).max() < 1e-11 * wl.radius
 
 
-def fp32_position_floor(steps, u_interface):
-    """Bound on the vertex drift of the FP32 path, whose collision arithmetic is float (the
-    precision the FP32 form keeps): each step's float rounding of the collision puts about
-    1e-7 relative noise into u, a random walk of size 1e-7 sqrt(t) whose time integral is
-    (2/3) t^1.5 1e-7 |u|; doubled for margin. The source was isolated on the oracle over this
-    run (R = 6): with only its collision computed in float the vertices move by 1.2e-6 R at
-    most (2.6e-7 R on average), while rounding the stored populations, the nodal forces, the
-    spread field or the interpolated velocities to float moves them by 1.2e-9 R, 9e-11 R,
-    7e-11 R and 7e-10 R."""
-    return 2.0 * (2.0 / 3.0) * steps ** 1.5 * 1e-7 * u_interface
-
-
 def test_shear32_fp32_1000_steps():
-    """FP32 path after 1000 steps on the 32^3 shear workload: relative L2 <= 1e-5 on u and
-    rho. Vertices: the mean within 1e-6 R, the largest within the floor that float collision
-    arithmetic sets on this run (about 1.5e-6 R, above the 1e-6 R aimed at; the FP64 path
-    meets 1e-11 R on the same run, and the 64^3 FP32 run meets 1e-6 R)."""
+    """FP32 path after 1000 steps on the 32^3 shear workload, at the FP32 bars: relative L2
+    <= 1e-5 on u and rho, vertices within 1e-6 R of the FP64 oracle (measured on GB300: u 6.9e-7,
+    vertices 5.3e-7 R at most). The collision forms u = j'/rho with one residual correction;
+    with a plain float quotient the vertices drifted to 1.5e-6 R here. rho - rho0, a field of
+    deviations near 1e-5 that float storage resolves to about 1e-10, is held to 2e-5 relative
+    (measured 1.2e-5)."""
     wl, ref, gpu = _shear_run("fp32", 1000)
     r0, u0 = ref.fields()
     r1, u1 = gpu.fields()
     assert rel_l2(u1, u0) < 1e-5
     assert rel_l2(r1, r0) < 1e-5
+    assert rel_l2(r1 - 1, r0 - 1) < 2e-5
     dq = np.abs(gpu.vertices() - ref.vertices())
-    gamma = (wl.wall_u_top[0] - wl.wall_u_bottom[0]) / (wl.nz - 2)
-    assert dq.max() < fp32_position_floor(1000, gamma * wl.radius)
-    assert dq.mean() < 1e-6 * wl.radius
+    assert dq.max() < 1e-6 * wl.radius
 
 
 def test_shear64_fp32_1000_steps():
