@@ -62,7 +62,9 @@ typedef struct {
   int32_t z_periodic;      /* 0: bounce-back walls at both z ends; 1: periodic z (tests) */
   int32_t ib_sms;          /* SMs given to the interface chain of iblb_step as a partition of
                               the GPU (green context); the stream-collide passes get the rest.
-                              0: 32, or 40 with 16-bit storage (rounded to the device's
+                              0: when the stream-collide pass moves at least 1 GiB
+                              (2 x 19 x nx ny nz x storage bytes) 32, or 40 with 16-bit
+                              storage; below that 64 (rounded to the device's
                               partition granularity), < 0: no
                               partition (both share all SMs, interface stream at top priority).
                               If the device or driver cannot partition, no partition is used. */

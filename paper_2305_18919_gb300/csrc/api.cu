@@ -308,9 +308,16 @@ int iblb_create(const iblb_lattice_desc *d, void *cuda_stream, iblb_ctx **out) {
   // between the blocks of the full-lattice pass instead of after it.
   int prio_lo = 0, prio_hi = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
-  // 16-bit storage halves the lattice pass's bytes: it needs fewer SMs than the interface
-  // chain then does (measured on the 256^3 workload: 40 of 152 SMs for 16-bit, 32 otherwise)
-  const int want = d->ib_sms != 0 ? d->ib_sms : (c.pop_size == 2 ? 40 : 32);
+  // Default split, from sweeps of the interface SMs. A full-lattice pass of at least 1 GiB
+  // hides the interface chain on 32 SMs (256^3 FP32, 2.5 GB: 39.5k MLUPS against 34.8k
+  // unpartitioned); 16-bit storage halves the pass, so the chain takes 40 (256^3 FP16: 64.9k
+  // against 55.8k on 32 SMs). A shorter pass leaves the chain as the critical path, which then
+  // takes 64 SMs (128x128x96 FP32 wetting, 1.5 M nodes: 0.090 ms against 0.115 ms on 32 SMs;
+  // 32^3 FP64 shear: 0.136 ms against 0.138 ms on 32 and 0.149 ms unpartitioned).
+  const size_t pass_bytes = (size_t)2 * iblb::Q * c.ncell * c.pop_size;
+  const int want = d->ib_sms != 0 ? d->ib_sms
+                   : pass_bytes < ((size_t)1 << 30) ? 64
+                   : (c.pop_size == 2 ? 40 : 32);
   if (e == cudaSuccess && !(want > 0 && make_partitions(c, want, prio_hi))) {
     e = cudaStreamCreateWithPriority(&c.ib, cudaStreamNonBlocking, prio_hi);
     c.ls = c.stream;
@@ -342,7 +349,7 @@ void iblb_destroy(iblb_ctx *h) {
     dfree(c.out_src[b]);
     dfree(c.Fslot[b]);
   }
-  dfree(c.counters); dfree(c.slot_count); dfree(c.src_index); dfree(c.Rslot); dfree(c.bucket); dfree(c.spill_bits); dfree(c.Uslot);
+  dfree(c.counters); dfree(c.slot_count); dfree(c.src_index); dfree(c.Rslot); dfree(c.bucket); dfree(c.spill_bits); dfree(c.Uslot); dfree(c.pair_list);
   dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.xref); dfree(c.fgeo); dfree(c.disp); dfree(c.vf_start); dfree(c.vf_list);
   dfree(c.fcontrib); dfree(c.fnorm); dfree(c.vol_partial); dfree(c.phi); dfree(c.gvol); dfree(c.stencil);
   dfree(c.dscratch);
@@ -398,6 +405,9 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
     for (int j = 0; j < nf; j++)
       for (int k = 0; k < 3; k++) vf_list[fill[faces[3 * j + k]]++] = 3 * j + k;
   }
+  // the force-pair list indexes slot * 32 + pair in an int: at most 2^26 tile slots
+  if ((long)(8L * nv < (long)c.ntiles ? 8L * nv : (long)c.ntiles) > (1L << 26))
+    return fail(c, IBLB_ECAPACITY, "mesh too large: more than 2^26 interface tile slots");
   c.nv = nv;
   c.nf = nf;
   c.V0 = V0;
@@ -437,6 +447,7 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
     CUDA_TRY(c, cudaMemsetAsync(c.tile_slot[b], 0xff, c.ntiles * sizeof(int), c.stream));
   }
   CUDA_TRY(c, dalloc(&c.slot_count, (size_t)c.max_slots));
+  CUDA_TRY(c, dalloc(&c.pair_list, (size_t)32 * c.max_slots));
   CUDA_TRY(c, dalloc(&c.src_index, (size_t)c.max_slots));
   c.max_sources = nv < c.max_slots ? nv : c.max_slots;  // a source tile holds >= 1 vertex base
   CUDA_TRY(c, dalloc_bytes(&c.Rslot, (size_t)c.max_sources * 343 * 4 * rs));

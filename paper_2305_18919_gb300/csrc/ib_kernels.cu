@@ -197,6 +197,7 @@ __device__ __forceinline__ void face_body(const FaceArgs<real> &A, int bid, int 
   if (bid == 0 && threadIdx.x == 0) {
     A.ovf_count[0] = 0;  // vertices beyond their bucket (a count only)
     A.ovf_count[2] = 0;  // number of source tiles (counters[4])
+    A.ovf_count[3] = 0;  // listed force pairs (counters[5]), appended by K4b
   }
   for (int w = bid * blockDim.x + threadIdx.x; w < A.spill_words; w += nb * blockDim.x)
     A.spill_bits[w] = 0u;
@@ -565,6 +566,7 @@ struct GatherArgs {
   const int *slot_tile, *nslots_ptr, *out_src;
   const Vec4<real> *Rslot;
   Vec4<real> *Fslot;
+  int *pair_list, *npairs;  // node pairs (x even, x + 1) with a force, for K1t
   Dims D;
 };
 
@@ -598,6 +600,17 @@ __device__ __forceinline__ void spread_gather_body(const GatherArgs<real> &A, in
     o.z = drop ? real(0) : f[2];
     o.w = real(0);
     Fslot[(size_t)b * TILE_CELLS + tid] = o;
+    // list the pairs (tid even, tid + 1) of this warp with a non-zero force on either node:
+    // one atomic per warp, entries in pair order within the warp
+    const bool has = o.x != real(0) || o.y != real(0) || o.z != real(0);
+    const unsigned m = __ballot_sync(0xffffffffu, has);
+    const unsigned pm = (m | (m >> 1)) & 0x55555555u;  // bit 2k: pair k has a force
+    const int lane = tid & 31;
+    int base = 0;
+    if (lane == 0 && pm) base = atomicAdd(A.npairs, __popc(pm));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((pm >> lane) & 1u)
+      A.pair_list[base + __popc(pm & ((1u << lane) - 1u))] = 32 * b + (tid >> 1);
   }
 }
 
@@ -907,6 +920,7 @@ __global__ void clear_counts_kernel(const int *__restrict__ nslots, int *__restr
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ovf_count[0] = 0;
     ovf_count[2] = 0;
+    ovf_count[3] = 0;
   }
 }
 
@@ -1067,6 +1081,8 @@ GatherArgs<real> gather_args(const Ctx &c) {
   a.out_src = c.out_src[c.map];
   a.Rslot = (const Vec4<real> *)c.Rslot;
   a.Fslot = (Vec4<real> *)c.Fslot[c.map];
+  a.pair_list = c.pair_list;
+  a.npairs = c.counters + 5;
   a.D = dims_of(c);
   return a;
 }

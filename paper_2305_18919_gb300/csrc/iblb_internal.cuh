@@ -125,7 +125,8 @@ struct Ctx {
   int tile_estimate = 0;  // active tiles expected for the mesh (sizes the batched grids)
   int *tile_slot[2] = {nullptr, nullptr};  // [ntiles] slot or -1
   int *slot_tile[2] = {nullptr, nullptr};  // [max_slots] tile id of each active slot
-  int *counters = nullptr;  // [0..1] nslots per map, [2] spilled vertices, [3] health, [4] sources
+  int *counters = nullptr;  // [0..1] nslots per map, [2] spilled vertices, [3] health, [4] sources,
+                            // [5] listed force pairs
   int *src_index = nullptr;                // [max_slots] region of a source tile (slot)
   void *Rslot = nullptr;                   // [max_sources][343] Vec4 spreading regions
   int *out_src[2] = {nullptr, nullptr};    // per map: [max_slots][8] region of source T - e
@@ -137,6 +138,8 @@ struct Ctx {
   int spill_words = 0;                     // (nv + 31) / 32
   void *Fslot[2] = {nullptr, nullptr};     // per map: [max_slots][64] Vec4 force density
   void *Uslot = nullptr;                   // [max_slots][64] Vec4 velocity
+  int *pair_list = nullptr;                // [32 max_slots] slot * 32 + pair: the node pairs with
+                                           //   a non-zero force (K4b appends, K1t reads)
   int map = 0;                             // tile map of the current vertex positions
   // mesh
   int nv = 0, nf = 0;

@@ -1018,33 +1018,50 @@ __global__ void __launch_bounds__(128, MultiMinBlocks<real, S>::value) stream_co
 //   D_i = omega (f^eq_i(rho, uF) - f^eq_i(rho, u0)) + S_i(uF, g + F) - S_i(u0, g),
 //   uF = u0 + F/(2 rho).
 // K1t therefore reads and writes only each node's own populations, no pulled neighbours.
-// A warp takes an x-pair of tiles (tx even, tx + 1) when both are active, else one tile;
-// each thread a node pair (x0, x0 + 1) of an 8-node row, idle where its tile is not active.
-// Node pairs whose interface force is zero keep K1's result, which is already final.
+// Its work list is the node pairs (x0, x0 + 1), x0 even, of the active tiles that carry a
+// non-zero force, appended by the spreading's gather pass (K4b) as slot * 32 + pair; one
+// thread per listed pair. Pairs without force keep K1's result, which is already final.
 template <typename real, typename S>
 struct TilesArgs {
   S *fout;
-  const int *slot_tile, *nslots_ptr, *tile_slot;
+  const int *slot_tile, *pair_list, *npairs_ptr;
   const Vec4<real> *Fslot;
   LatParams<real> P;
-  int max_slots;
+  int max_pairs;
 };
 
 // f (deviations, after the collision with the body force g alone) becomes the collision
-// with g + F; see K1t above. Opposite directions are handled in symmetric/antisymmetric
-// pairs as in collide().
+// with g + F; see K1t above. D is a quadratic form in the lattice vector: for a direction i
+// and its opposite,
+//   D_i = w_i (c_i^T M c_i + q0 + c_i . v),   D_opp(i) = w_i (c_i^T M c_i + q0 - c_i . v),
+//   M = 9/4 omega rho (dl s^T + s dl^T) + 9/2 gamma (Ft uF^T + uF Ft^T - g u0^T - u0 g^T),
+//   v = 3 (omega rho dl + gamma F),  dl = uF - u0,  s = uF + u0,  Ft = g + F,
+// so a node needs ten numbers (M's diagonal, twice its off-diagonal, q0, v) once its
+// moments are known, and each direction a few adds.
 template <typename real>
-__device__ __forceinline__ void force_correction(real f[Q], const real F[3],
-                                                 const LatParams<real> &P) {
-  real drho = f[0], Jx = 0, Jy = 0, Jz = 0;
-#pragma unroll
-  for (int i = 1; i < Q; i += 2) {
-    drho += f[i] + f[i + 1];
-    const real d = f[i] - f[i + 1];
-    if (cx(i)) Jx += cx(i) > 0 ? d : -d;
-    if (cy(i)) Jy += cy(i) > 0 ? d : -d;
-    if (cz(i)) Jz += cz(i) > 0 ? d : -d;
+struct Correction {
+  real dx, dy, dz;     // M_aa
+  real oxy, oxz, oyz;  // 2 M_ab
+  real q0;             // -1.5 omega rho (uF^2 - u0^2) - 3 gamma (uF.Ft - u0.g)
+  real vx, vy, vz;
+};
+
+// Moments of K1's output at one node: drho = sum f, J = sum c f (deviations).
+template <typename real>
+struct Moments {
+  real drho = 0, Jx = 0, Jy = 0, Jz = 0;
+  __device__ __forceinline__ void add(int i, real f) {
+    drho += f;
+    if (cx(i)) Jx += cx(i) > 0 ? f : -f;
+    if (cy(i)) Jy += cy(i) > 0 ? f : -f;
+    if (cz(i)) Jz += cz(i) > 0 ? f : -f;
   }
+};
+
+template <typename real>
+__device__ __forceinline__ Correction<real> correction_of(const Moments<real> &m, const real F[3],
+                                                         const LatParams<real> &P) {
+  const real drho = m.drho, Jx = m.Jx, Jy = m.Jy, Jz = m.Jz;
   const real rho = P.rho0 + drho;
   const real ir = real(1) / rho;
   const real u0[3] = {(Jx - real(0.5) * P.g[0]) * ir, (Jy - real(0.5) * P.g[1]) * ir,
@@ -1053,29 +1070,39 @@ __device__ __forceinline__ void force_correction(real f[Q], const real F[3],
   const real uF[3] = {u0[0] + dl[0], u0[1] + dl[1], u0[2] + dl[2]};
   const real sm[3] = {uF[0] + u0[0], uF[1] + u0[1], uF[2] + u0[2]};
   const real Ft[3] = {P.g[0] + F[0], P.g[1] + F[1], P.g[2] + F[2]};
-  const real orho = P.omega * rho;
-  const real gm = P.guo;
-  // the direction-independent part: -1.5 omega rho (uF^2 - u0^2) - 3 gamma (uF.Ft - u0.g)
-  const real q0 = real(-1.5) * orho * (dl[0] * sm[0] + dl[1] * sm[1] + dl[2] * sm[2]) -
-                  real(3) * gm *
-                      ((uF[0] * Ft[0] + uF[1] * Ft[1] + uF[2] * Ft[2]) -
-                       (u0[0] * P.g[0] + u0[1] * P.g[1] + u0[2] * P.g[2]));
-  f[0] += real(wgt(0)) * q0;
-#pragma unroll
-  for (int i = 1; i < Q; i += 2) {
-    const real w = (real)wgt(i);
-    const real cd = cx(i) * dl[0] + cy(i) * dl[1] + cz(i) * dl[2];
-    const real cs = cx(i) * sm[0] + cy(i) * sm[1] + cz(i) * sm[2];
-    const real cuF = cx(i) * uF[0] + cy(i) * uF[1] + cz(i) * uF[2];
-    const real cu0 = cx(i) * u0[0] + cy(i) * u0[1] + cz(i) * u0[2];
-    const real cFt = cx(i) * Ft[0] + cy(i) * Ft[1] + cz(i) * Ft[2];
-    const real cg = cx(i) * P.g[0] + cy(i) * P.g[1] + cz(i) * P.g[2];
-    const real cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
-    const real sym = w * (real(4.5) * orho * cd * cs + real(9) * gm * (cFt * cuF - cg * cu0) + q0);
-    const real asym = w * real(3) * (orho * cd + gm * cF);
-    f[i] += sym + asym;
-    f[i + 1] += sym - asym;
-  }
+  const real a = real(4.5) * P.omega * rho, b = real(9) * P.guo;
+  Correction<real> k;
+  k.q0 = real(-1.5) * P.omega * rho * (dl[0] * sm[0] + dl[1] * sm[1] + dl[2] * sm[2]) -
+         real(3) * P.guo *
+             ((uF[0] * Ft[0] + uF[1] * Ft[1] + uF[2] * Ft[2]) -
+              (u0[0] * P.g[0] + u0[1] * P.g[1] + u0[2] * P.g[2]));
+  k.dx = a * dl[0] * sm[0] + b * (Ft[0] * uF[0] - P.g[0] * u0[0]);
+  k.dy = a * dl[1] * sm[1] + b * (Ft[1] * uF[1] - P.g[1] * u0[1]);
+  k.dz = a * dl[2] * sm[2] + b * (Ft[2] * uF[2] - P.g[2] * u0[2]);
+  k.oxy = a * (dl[0] * sm[1] + dl[1] * sm[0]) +
+          b * (Ft[0] * uF[1] + Ft[1] * uF[0] - P.g[0] * u0[1] - P.g[1] * u0[0]);
+  k.oxz = a * (dl[0] * sm[2] + dl[2] * sm[0]) +
+          b * (Ft[0] * uF[2] + Ft[2] * uF[0] - P.g[0] * u0[2] - P.g[2] * u0[0]);
+  k.oyz = a * (dl[1] * sm[2] + dl[2] * sm[1]) +
+          b * (Ft[1] * uF[2] + Ft[2] * uF[1] - P.g[1] * u0[2] - P.g[2] * u0[1]);
+  const real oa = P.omega * rho;
+  k.vx = real(3) * (oa * dl[0] + P.guo * F[0]);
+  k.vy = real(3) * (oa * dl[1] + P.guo * F[1]);
+  k.vz = real(3) * (oa * dl[2] + P.guo * F[2]);
+  return k;
+}
+
+// D_i of one node (i and its opposite share M and v; c_opp = -c_i flips only c_i . v).
+template <typename real>
+__device__ __forceinline__ real correction_delta(int i, const Correction<real> &k) {
+  real quad = k.q0, lin = 0;
+  if (cx(i)) { quad += k.dx; lin += cx(i) > 0 ? k.vx : -k.vx; }
+  if (cy(i)) { quad += k.dy; lin += cy(i) > 0 ? k.vy : -k.vy; }
+  if (cz(i)) { quad += k.dz; lin += cz(i) > 0 ? k.vz : -k.vz; }
+  if (cx(i) && cy(i)) quad += cx(i) * cy(i) > 0 ? k.oxy : -k.oxy;
+  if (cx(i) && cz(i)) quad += cx(i) * cz(i) > 0 ? k.oxz : -k.oxz;
+  if (cy(i) && cz(i)) quad += cy(i) * cz(i) > 0 ? k.oyz : -k.oyz;
+  return real(wgt(i)) * (quad + lin);
 }
 
 template <typename real, typename S>
@@ -1083,48 +1110,41 @@ __device__ __forceinline__ void tiles_body(const TilesArgs<real, S> &A, int bid,
   using V2 = typename Storage<S>::V2;
   S *__restrict__ fout = A.fout;
   const int *__restrict__ slot_tile = A.slot_tile;
-  const int *__restrict__ tile_slot = A.tile_slot;
+  const int *__restrict__ pair_list = A.pair_list;
   const Vec4<real> *__restrict__ Fslot = A.Fslot;
   const LatParams<real> P = A.P;  // held in registers: the loop below is latency-bound
-  const int nslots = min(*A.nslots_ptr, A.max_slots);
-  const int lane = threadIdx.x & 31;
-  const int xq = lane & 3, ly = (lane >> 2) & 3;  // node pair 2 xq, 2 xq + 1 of an 8-node row
-  const int half = xq >> 1;                         // 0: the even tile, 1: the odd tile
-  const int warps = blockDim.x >> 5;
-  for (int s = bid * warps + (threadIdx.x >> 5); s < nslots; s += nb * warps) {
+  const int npairs = min(*A.npairs_ptr, A.max_pairs);
+  for (int k = bid * blockDim.x + threadIdx.x; k < npairs; k += nb * blockDim.x) {
+    const int e = pair_list[k];
+    const int s = e >> 5, cell = 2 * (e & 31);  // slot, and the pair's first node in the tile
+    const Vec4<real> Fa = Fslot[(size_t)s * TILE_CELLS + cell];
+    const Vec4<real> Fb = Fslot[(size_t)s * TILE_CELLS + cell + 1];
     const int t = slot_tile[s];
     const int tx = t % P.ntx, ty = (t / P.ntx) % P.nty, tz = t / (P.ntx * P.nty);
-    const int px = tx ^ 1;
-    const int sp = px < P.ntx ? tile_slot[t - tx + px] : -1;
-    if (sp >= 0 && (tx & 1)) continue;  // an active pair is taken from its even tile
-    const int sl = (tx & 1) ? -1 : s, sr = (tx & 1) ? s : sp;
-    const int ss = half ? sr : sl;
-    if (ss < 0) continue;  // this half of the pair is not active
-    const int x0 = (tx & ~1) * TILE + 2 * xq, y = ty * TILE + ly;
-    for (int h = 0; h < 2; h++) {
-      const int lz = (lane >> 4) + 2 * h;
-      const int z = tz * TILE + lz;
-      if (z >= P.nz || (P.has_walls && (z == 0 || z == P.nz - 1))) continue;
-      const int cell = 16 * lz + 4 * ly + 2 * (xq & 1);
-      const Vec4<real> Fa = Fslot[(size_t)ss * TILE_CELLS + cell];
-      const Vec4<real> Fb = Fslot[(size_t)ss * TILE_CELLS + cell + 1];
-      if (Fa.x == real(0) && Fa.y == real(0) && Fa.z == real(0) && Fb.x == real(0) &&
-          Fb.y == real(0) && Fb.z == real(0))
-        continue;
-      const size_t n = (size_t)z * P.nx * P.ny + (size_t)y * P.nx + x0;
-      real a[Q], b[Q];
+    const int x0 = tx * TILE + (cell & 3), y = ty * TILE + ((cell >> 2) & 3);
+    const int z = tz * TILE + (cell >> 4);
+    if (z >= P.nz || (P.has_walls && (z == 0 || z == P.nz - 1))) continue;
+    const size_t n = (size_t)z * P.nx * P.ny + (size_t)y * P.nx + x0;
+    real a[Q], b[Q];
+    Moments<real> ma, mb;
 #pragma unroll
-      for (int i = 0; i < Q; i++) {
-        widen2(*reinterpret_cast<const V2 *>(fout + (size_t)i * P.ncell + n), a[i], b[i]);
-        a[i] *= real(kinv<S>(i));
-        b[i] *= real(kinv<S>(i));
-      }
-      const real FA[3] = {Fa.x, Fa.y, Fa.z};
-      const real FB[3] = {Fb.x, Fb.y, Fb.z};
-      force_correction<real>(a, FA, P);
-      force_correction<real>(b, FB, P);
-      store_pair(fout, P, n, a, b);
+    for (int i = 0; i < Q; i++) {
+      widen2(*reinterpret_cast<const V2 *>(fout + (size_t)i * P.ncell + n), a[i], b[i]);
+      a[i] *= real(kinv<S>(i));
+      b[i] *= real(kinv<S>(i));
+      ma.add(i, a[i]);
+      mb.add(i, b[i]);
     }
+    const real FA[3] = {Fa.x, Fa.y, Fa.z};
+    const real FB[3] = {Fb.x, Fb.y, Fb.z};
+    const Correction<real> ka = correction_of<real>(ma, FA, P);
+    const Correction<real> kb = correction_of<real>(mb, FB, P);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      a[i] += correction_delta<real>(i, ka);
+      b[i] += correction_delta<real>(i, kb);
+    }
+    store_pair(fout, P, n, a, b);
   }
 }
 
@@ -1451,18 +1471,18 @@ TilesArgs<real, S> tiles_args(const Ctx &c) {
   TilesArgs<real, S> a;
   a.fout = (S *)c.f[c.cur ^ 1];
   a.slot_tile = c.slot_tile[c.map];
-  a.nslots_ptr = c.counters + c.map;
-  a.tile_slot = c.tile_slot[c.map];
+  a.pair_list = c.pair_list;
+  a.npairs_ptr = c.counters + 5;
   a.Fslot = (const Vec4<real> *)c.Fslot[c.map];
   a.P = lat_params<real>(c);
-  a.max_slots = c.max_slots;
+  a.max_pairs = 32 * c.max_slots;
   return a;
 }
-// 4 tiles per block; single context: up to ~4900 active tiles in one pass; in a batch one
-// warp per two of the context's expected active tiles
+// a thread per listed pair; single context: four 128-thread blocks per SM (about 78k pairs
+// in one pass); in a batch a block per eight of the context's expected active tiles
 int tiles_blocks(const Ctx &c, bool batched) {
-  int grid = batched ? (c.tile_estimate + 7) / 8 : c.sm_count * 8;
-  if (4 * grid > c.max_slots) grid = (c.max_slots + 3) / 4;
+  int grid = batched ? (c.tile_estimate + 7) / 8 : c.sm_count * 4;
+  if (grid > c.max_slots) grid = c.max_slots;
   return grid < 1 ? 1 : grid;
 }
 
