@@ -456,6 +456,8 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
   CUDA_TRY(c, dalloc(&c.spill_bits, (size_t)c.spill_words));
   CUDA_TRY(c, cudaMemsetAsync(c.spill_bits, 0, (size_t)c.spill_words * sizeof(unsigned), c.stream));
   CUDA_TRY(c, dalloc_bytes(&c.Uslot, (size_t)c.max_slots * 4 * iblb::TILE_CELLS * rs));
+  // only the listed (stencil) nodes are written each step, and only they are read
+  CUDA_TRY(c, cudaMemsetAsync(c.Uslot, 0, (size_t)c.max_slots * 4 * iblb::TILE_CELLS * rs, c.stream));
   CUDA_TRY(c, cudaMemsetAsync(c.counters, 0, 8 * sizeof(int), c.stream));
   CUDA_TRY(c, cudaMemsetAsync(c.qdot, 0, (size_t)3 * nv * sizeof(double), c.stream));
   CUDA_TRY(c, cudaMemcpyAsync(c.q, verts, (size_t)3 * nv * sizeof(double), cudaMemcpyHostToDevice, c.stream));

@@ -488,6 +488,7 @@ __device__ __forceinline__ void spread_source_body(const SourceArgs<real> &A, in
           o.x += w * f.x;
           o.y += w * f.y;
           o.z += w * f.z;
+          o.w = real(1);  // a stencil node of some vertex (the interpolation reads it)
         }
         __syncwarp();
       }
@@ -531,6 +532,7 @@ __device__ __forceinline__ void spread_source_body(const SourceArgs<real> &A, in
               o.x += w * fx;
               o.y += w * fy;
               o.z += w * fz;
+              o.w = real(1);
             }
             __syncwarp();
           }
@@ -560,13 +562,15 @@ __global__ void __launch_bounds__(32 * SrcWarps<real>::value) spread_source_kern
 // node (lx, ly, lz): the force is the sum, in the fixed order e = 0..7, of the regions of the
 // source tiles S = T - e pushed by K4a; the node sits at (l + 4 e) in S's region. On a
 // periodic axis only 4 nodes long S - e and S coincide and the two terms are the node's two
-// images in the region. Force landing on a wall layer is dropped.
+// images in the region. Force landing on a wall layer is dropped. K4a marks each region
+// node that lies in a vertex's stencil (w = 1); K4b lists the node pairs holding such a node,
+// the work of the active-tile correction (K1t) and of the shell velocity (K1b).
 template <typename real>
 struct GatherArgs {
   const int *slot_tile, *nslots_ptr, *out_src;
   const Vec4<real> *Rslot;
   Vec4<real> *Fslot;
-  int *pair_list, *npairs;  // node pairs (x even, x + 1) with a force, for K1t
+  int *pair_list, *npairs;  // node pairs (x even, x + 1) in some vertex's stencil, for K1t, K1b
   Dims D;
 };
 
@@ -583,6 +587,7 @@ __device__ __forceinline__ void spread_gather_body(const GatherArgs<real> &A, in
   for (int b = bid; b < nslots; b += nb) {
     const int *src = out_src + 8 * (size_t)b;
     real f[3] = {0, 0, 0};
+    bool stencil_node = false;
     for (int e = 0; e < 8; e++) {
       const int reg = src[e];
       const int rx = lx + 4 * (e & 1), ry = ly + 4 * ((e >> 1) & 1), rz = lz + 4 * (e >> 2);
@@ -591,6 +596,7 @@ __device__ __forceinline__ void spread_gather_body(const GatherArgs<real> &A, in
       f[0] += r.x;
       f[1] += r.y;
       f[2] += r.z;
+      stencil_node |= r.w != real(0);
     }
     const int Z = (slot_tile[b] / (D.ntx * D.nty)) * TILE + lz;
     const bool drop = D.has_walls && (Z == 0 || Z >= D.nz - 1);
@@ -600,11 +606,12 @@ __device__ __forceinline__ void spread_gather_body(const GatherArgs<real> &A, in
     o.z = drop ? real(0) : f[2];
     o.w = real(0);
     Fslot[(size_t)b * TILE_CELLS + tid] = o;
-    // list the pairs (tid even, tid + 1) of this warp with a non-zero force on either node:
-    // one atomic per warp, entries in pair order within the warp
-    const bool has = o.x != real(0) || o.y != real(0) || o.z != real(0);
-    const unsigned m = __ballot_sync(0xffffffffu, has);
-    const unsigned pm = (m | (m >> 1)) & 0x55555555u;  // bit 2k: pair k has a force
+    // list the pairs (tid even, tid + 1) of this warp of which either node is a fluid node of
+    // some vertex's stencil (every node that can carry a force, and every node the
+    // interpolation reads off the wall layers): one atomic per warp, entries in pair order
+    // within the warp
+    const unsigned m = __ballot_sync(0xffffffffu, stencil_node && !drop);
+    const unsigned pm = (m | (m >> 1)) & 0x55555555u;  // bit 2k: pair k is listed
     const int lane = tid & 31;
     int base = 0;
     if (lane == 0 && pm) base = atomicAdd(A.npairs, __popc(pm));

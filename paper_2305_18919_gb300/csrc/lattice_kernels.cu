@@ -1018,9 +1018,9 @@ __global__ void __launch_bounds__(128, MultiMinBlocks<real, S>::value) stream_co
 //   D_i = omega (f^eq_i(rho, uF) - f^eq_i(rho, u0)) + S_i(uF, g + F) - S_i(u0, g),
 //   uF = u0 + F/(2 rho).
 // K1t therefore reads and writes only each node's own populations, no pulled neighbours.
-// Its work list is the node pairs (x0, x0 + 1), x0 even, of the active tiles that carry a
-// non-zero force, appended by the spreading's gather pass (K4b) as slot * 32 + pair; one
-// thread per listed pair. Pairs without force keep K1's result, which is already final.
+// Its work list is the node pairs (x0, x0 + 1), x0 even, that hold a node of some vertex's
+// stencil, appended by the spreading's gather pass (K4b) as slot * 32 + pair; one thread per
+// listed pair. Pairs without force keep K1's result, which is already final.
 template <typename real, typename S>
 struct TilesArgs {
   S *fout;
@@ -1119,6 +1119,9 @@ __device__ __forceinline__ void tiles_body(const TilesArgs<real, S> &A, int bid,
     const int s = e >> 5, cell = 2 * (e & 31);  // slot, and the pair's first node in the tile
     const Vec4<real> Fa = Fslot[(size_t)s * TILE_CELLS + cell];
     const Vec4<real> Fb = Fslot[(size_t)s * TILE_CELLS + cell + 1];
+    if (Fa.x == real(0) && Fa.y == real(0) && Fa.z == real(0) && Fb.x == real(0) &&
+        Fb.y == real(0) && Fb.z == real(0))
+      continue;
     const int t = slot_tile[s];
     const int tx = t % P.ntx, ty = (t / P.ntx) % P.nty, tz = t / (P.ntx * P.nty);
     const int x0 = tx * TILE + (cell & 3), y = ty * TILE + ((cell >> 2) & 3);
@@ -1160,77 +1163,70 @@ __global__ void __launch_bounds__(128) stream_collide_tiles_kernel_multi(
   tiles_body<real, S>(all[m.inst], m.block, m.nblocks);
 }
 
-// K1b: velocity after streaming at every node of the active interface tiles.
-// One 64-thread block per active tile (grid-stride over the device-side tile count).
+// K1b: velocity after streaming at the nodes the interpolation reads: the nodes of the pairs
+// that K4b listed (every fluid node of a vertex's stencil, and its pair partner); one thread
+// per node of a listed pair. u = (j + (g + F)/2)/rho, the velocity of the forced collision
+// (Eq. 10 with Guo's forcing). The wall layers, which the interpolation takes from the wall
+// velocities, are never listed.
 template <typename real, typename S>
 struct ShellArgs {
   const S *fpost;
-  const int *slot_tile, *nslots_ptr;
+  const int *slot_tile, *pair_list, *npairs_ptr;
   const Vec4<real> *Fslot;
   Vec4<real> *Uslot;
   LatParams<real> P;
-  real ubx, uby, ubz, utx, uty, utz;
-  int max_slots;
+  int max_pairs;
 };
 
 template <typename real, typename S>
 __device__ __forceinline__ void shell_body(const ShellArgs<real, S> &A, int bid, int nb) {
   const S *__restrict__ fpost = A.fpost;
   const int *__restrict__ slot_tile = A.slot_tile;
+  const int *__restrict__ pair_list = A.pair_list;
   const Vec4<real> *__restrict__ Fslot = A.Fslot;
   Vec4<real> *__restrict__ Uslot = A.Uslot;
   const LatParams<real> P = A.P;
-  const real ubx = A.ubx, uby = A.uby, ubz = A.ubz, utx = A.utx, uty = A.uty, utz = A.utz;
-  const int nslots = min(*A.nslots_ptr, A.max_slots);
-  const int cell = threadIdx.x;
-  for (int s = bid; s < nslots; s += nb) {
+  const int nodes = 2 * min(*A.npairs_ptr, A.max_pairs);
+  for (int k = bid * blockDim.x + threadIdx.x; k < nodes; k += nb * blockDim.x) {
+    const int e = pair_list[k >> 1];
+    const int s = e >> 5, cell = 2 * (e & 31) + (k & 1);
     const int t = slot_tile[s];
     const int tx = t % P.ntx, ty = (t / P.ntx) % P.nty, tz = t / (P.ntx * P.nty);
     const int x = tx * TILE + (cell & 3), y = ty * TILE + ((cell >> 2) & 3),
               z = tz * TILE + (cell >> 4);
-    real u[3] = {0, 0, 0};
-    if (z < P.nz) {
-      if (P.has_walls && z == 0) {
-        u[0] = ubx; u[1] = uby; u[2] = ubz;
-      } else if (P.has_walls && z == P.nz - 1) {
-        u[0] = utx; u[1] = uty; u[2] = utz;
-      } else {
-        real f[Q];
-        pull(fpost, P, x, y, z, f);
-        real drho = 0, j[3] = {0, 0, 0};
+    if (z >= P.nz || (P.has_walls && (z == 0 || z == P.nz - 1))) continue;
+    real f[Q];
+    pull(fpost, P, x, y, z, f);
+    real drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
-        for (int i = 0; i < Q; i++) {
-          drho += f[i];
-          j[0] += cx(i) * f[i];
-          j[1] += cy(i) * f[i];
-          j[2] += cz(i) * f[i];
-        }
-        const Vec4<real> Fs = Fslot[(size_t)s * TILE_CELLS + cell];
-        const real Fk[3] = {Fs.x, Fs.y, Fs.z};
-        const real rho_hi = P.rho0 + drho;
-        const real rho_lo = (P.rho0 - rho_hi) + drho;
-        const real r1 = real(1) / rho_hi;
-        const real inv_rho = r1 * (real(1) - rho_lo * r1);
-        for (int k = 0; k < 3; k++)
-          u[k] = (j[k] + real(0.5) * (P.g[k] + Fk[k])) * inv_rho;
-      }
+    for (int i = 0; i < Q; i++) {
+      drho += f[i];
+      j[0] += cx(i) * f[i];
+      j[1] += cy(i) * f[i];
+      j[2] += cz(i) * f[i];
     }
+    const Vec4<real> Fs = Fslot[(size_t)s * TILE_CELLS + cell];
+    const real Fk[3] = {Fs.x, Fs.y, Fs.z};
+    const real rho_hi = P.rho0 + drho;
+    const real rho_lo = (P.rho0 - rho_hi) + drho;
+    const real r1 = real(1) / rho_hi;
+    const real inv_rho = r1 * (real(1) - rho_lo * r1);
     Vec4<real> uv;
-    uv.x = u[0];
-    uv.y = u[1];
-    uv.z = u[2];
+    uv.x = (j[0] + real(0.5) * (P.g[0] + Fk[0])) * inv_rho;
+    uv.y = (j[1] + real(0.5) * (P.g[1] + Fk[1])) * inv_rho;
+    uv.z = (j[2] + real(0.5) * (P.g[2] + Fk[2])) * inv_rho;
     uv.w = real(0);
     Uslot[(size_t)s * TILE_CELLS + cell] = uv;
   }
 }
 
 template <typename real, typename S>
-__global__ void __launch_bounds__(64) shell_velocity_kernel(const ShellArgs<real, S> A) {
+__global__ void __launch_bounds__(128) shell_velocity_kernel(const ShellArgs<real, S> A) {
   shell_body<real, S>(A, blockIdx.x, gridDim.x);
 }
 
 template <typename real, typename S>
-__global__ void __launch_bounds__(64) shell_velocity_kernel_multi(
+__global__ void __launch_bounds__(128) shell_velocity_kernel_multi(
     const ShellArgs<real, S> *__restrict__ all, const int *__restrict__ start, int n) {
   const MultiBlock m = multi_block(start, n);
   shell_body<real, S>(all[m.inst], m.block, m.nblocks);
@@ -1491,21 +1487,19 @@ ShellArgs<real, S> shell_args(const Ctx &c, const void *fpost) {
   ShellArgs<real, S> a;
   a.fpost = (const S *)fpost;
   a.slot_tile = c.slot_tile[c.map];
-  a.nslots_ptr = c.counters + c.map;
+  a.pair_list = c.pair_list;
+  a.npairs_ptr = c.counters + 5;
   a.Fslot = (const Vec4<real> *)c.Fslot[c.map];
   a.Uslot = (Vec4<real> *)c.Uslot;
   a.P = lat_params<real>(c);
-  a.ubx = (real)c.ub[0];
-  a.uby = (real)c.ub[1];
-  a.ubz = (real)c.ub[2];
-  a.utx = (real)c.ut[0];
-  a.uty = (real)c.ut[1];
-  a.utz = (real)c.ut[2];
-  a.max_slots = c.max_slots;
+  a.max_pairs = 32 * c.max_slots;
   return a;
 }
+// a thread per node of a listed pair, 128 per block; single context: sixteen blocks per SM of
+// the partition it runs on; in a batch a block per two of the context's expected active tiles
 int shell_blocks(const Ctx &c, bool batched) {
-  int grid = batched ? (c.tile_estimate + 1) / 2 : c.sm_count * 32;  // batched: per two tiles
+  const int sms = c.ib_sms > 0 ? c.ib_sms : c.sm_count;
+  int grid = batched ? (c.tile_estimate + 1) / 2 : sms * 16;
   if (grid > c.max_slots) grid = c.max_slots;
   return grid < 1 ? 1 : grid;
 }
@@ -1533,7 +1527,7 @@ cudaError_t stream_collide_tiles_t(Ctx &c, int first, cudaStream_t st) {
 
 template <typename real, typename S>
 cudaError_t shell_velocity_t(Ctx &c, cudaStream_t st) {
-  shell_velocity_kernel<real, S><<<shell_blocks(c, false), TILE_CELLS, 0, st>>>(
+  shell_velocity_kernel<real, S><<<shell_blocks(c, false), 128, 0, st>>>(
       shell_args<real, S>(c, c.f[c.cur]));
   return cudaGetLastError();
 }
@@ -1574,7 +1568,7 @@ cudaError_t lattice_launch_multi_t(MultiKernel k, const MultiLaunch &m, cudaStre
           (const TilesArgs<real, S> *)m.args, m.start, m.n);
       break;
     case MK_SHELL:
-      shell_velocity_kernel_multi<real, S><<<m.blocks, TILE_CELLS, 0, s>>>(
+      shell_velocity_kernel_multi<real, S><<<m.blocks, 128, 0, s>>>(
           (const ShellArgs<real, S> *)m.args, m.start, m.n);
       break;
     default:
