@@ -133,10 +133,66 @@ __device__ __forceinline__ real dev(const S *__restrict__ p, int i, size_t idx) 
   return real(widen(p[idx])) * real(kinv<S>(i));
 }
 
+// Loads of the shell-velocity pass, whose pulled rows are scattered over the lattice: the
+// prefetch-size qualifier bounds each L2 fill from DRAM to 64 bytes (a plain load brings a
+// whole 128-byte line for a 4-byte access). The pass runs beside the full-lattice pass, which
+// gets the DRAM bandwidth saved (256^3: 23.6 MB against 37.4 MB per launch).
+#define IBLB_SCATTER_LD "ld.global.L2::64B"
+__device__ __forceinline__ float ld_scattered(const float *p) {
+  float v;
+  asm(IBLB_SCATTER_LD ".f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_scattered(const double *p) {
+  double v;
+  asm(IBLB_SCATTER_LD ".f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ __half ld_scattered(const __half *p) {
+  unsigned short v;
+  asm(IBLB_SCATTER_LD ".b16 %0, [%1];" : "=h"(v) : "l"(p));
+  return __ushort_as_half(v);
+}
+__device__ __forceinline__ __nv_bfloat16 ld_scattered(const __nv_bfloat16 *p) {
+  unsigned short v;
+  asm(IBLB_SCATTER_LD ".b16 %0, [%1];" : "=h"(v) : "l"(p));
+  return __ushort_as_bfloat16(v);
+}
+__device__ __forceinline__ float2 ld_scattered(const float2 *p) {
+  float2 v;
+  asm(IBLB_SCATTER_LD ".v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double2 ld_scattered(const double2 *p) {
+  double2 v;
+  asm(IBLB_SCATTER_LD ".v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ __half2 ld_scattered(const __half2 *p) {
+  unsigned v;
+  asm(IBLB_SCATTER_LD ".b32 %0, [%1];" : "=r"(v) : "l"(p));
+  __half2 h;
+  memcpy(&h, &v, sizeof(v));
+  return h;
+}
+__device__ __forceinline__ __nv_bfloat162 ld_scattered(const __nv_bfloat162 *p) {
+  unsigned v;
+  asm(IBLB_SCATTER_LD ".b32 %0, [%1];" : "=r"(v) : "l"(p));
+  __nv_bfloat162 h;
+  memcpy(&h, &v, sizeof(v));
+  return h;
+}
+
+// dev() through ld_scattered
+template <typename real, typename S>
+__device__ __forceinline__ real dev_scattered(const S *__restrict__ p, int i, size_t idx) {
+  return real(widen(ld_scattered(p + idx))) * real(kinv<S>(i));
+}
+
 // Pull the 19 post-streaming populations of fluid node (x, y, z) from post-collision array
 // `fp`. A link whose source is a wall node is bounced back: the opposite post-collision
 // population of the same node plus the moving-wall term.
-template <typename real, typename S>
+template <typename real, typename S, bool SCATTERED = false>
 __device__ __forceinline__ void pull(const S *__restrict__ fp, const LatParams<real> &P, int x,
                                      int y, int z, real f[Q]) {
   const int xm = x == 0 ? P.nx - 1 : x - 1, xp = x == P.nx - 1 ? 0 : x + 1;
@@ -156,13 +212,12 @@ __device__ __forceinline__ void pull(const S *__restrict__ fp, const LatParams<r
   const size_t n = zo[1] + yo[1] + x;
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    if (cz(i) > 0 && wall_below) {
-      f[i] = dev<real>(fp, opp(i), (size_t)opp(i) * P.ncell + n) + P.wb[i];
-    } else if (cz(i) < 0 && wall_above) {
-      f[i] = dev<real>(fp, opp(i), (size_t)opp(i) * P.ncell + n) + P.wt[i];
-    } else {
-      f[i] = dev<real>(fp, i, (size_t)i * P.ncell + zo[1 - cz(i)] + yo[1 - cy(i)] + xo[1 - cx(i)]);
-    }
+    // (opposite directions have the same weight, so population i's scale serves both)
+    const bool bounce = (cz(i) > 0 && wall_below) || (cz(i) < 0 && wall_above);
+    const size_t idx = bounce ? (size_t)opp(i) * P.ncell + n
+                              : (size_t)i * P.ncell + zo[1 - cz(i)] + yo[1 - cy(i)] + xo[1 - cx(i)];
+    f[i] = SCATTERED ? dev_scattered<real>(fp, i, idx) : dev<real>(fp, i, idx);
+    if (bounce) f[i] += cz(i) > 0 ? P.wb[i] : P.wt[i];
   }
 }
 
@@ -1156,8 +1211,13 @@ __global__ void __launch_bounds__(128) stream_collide_tiles_kernel(const TilesAr
   tiles_body<real, S>(A, blockIdx.x, gridDim.x);
 }
 
+// the batched form reads its argument record as well: held to 128 registers (4 blocks per SM,
+// as the single-context kernel) for float arithmetic
+template <typename real>
+struct TilesMultiMinBlocks { static constexpr int value = sizeof(real) == 4 ? 4 : 1; };
+
 template <typename real, typename S>
-__global__ void __launch_bounds__(128) stream_collide_tiles_kernel_multi(
+__global__ void __launch_bounds__(128, TilesMultiMinBlocks<real>::value) stream_collide_tiles_kernel_multi(
     const TilesArgs<real, S> *__restrict__ all, const int *__restrict__ start, int n) {
   const MultiBlock m = multi_block(start, n);
   tiles_body<real, S>(all[m.inst], m.block, m.nblocks);
@@ -1196,7 +1256,7 @@ __device__ __forceinline__ void shell_body(const ShellArgs<real, S> &A, int bid,
               z = tz * TILE + (cell >> 4);
     if (z >= P.nz || (P.has_walls && (z == 0 || z == P.nz - 1))) continue;
     real f[Q];
-    pull(fpost, P, x, y, z, f);
+    pull<real, S, true>(fpost, P, x, y, z, f);
     real drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < Q; i++) {
