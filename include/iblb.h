@@ -125,6 +125,23 @@ int iblb_step(iblb_ctx *ctx, int32_t nsteps);
    each call. IBLB_EINVAL for every < 0. */
 int iblb_set_health_interval(iblb_ctx *ctx, int32_t every);
 
+/* Advance nsteps coupled steps like iblb_step, queued on the stream without any
+   synchronisation: the health word is not read by this call. A failed check of these steps is
+   returned (IBLB_EUNSTABLE, IBLB_ECAPACITY, IBLB_ETIMEOUT) by the next call that reads it:
+   iblb_read_vertices, iblb_read_vertex_velocities, iblb_read_fields, iblb_read_forces or
+   iblb_read_volume (in the same synchronisation as their own transfer; their output is
+   written all the same), iblb_check_health, iblb_step, iblb_read_force_field, the adjoint
+   calls or iblb_batch_step (before doing their own work, or in its status). Repeated calls
+   keep the first failure until it is read. iblb_init_equilibrium and iblb_load_state discard
+   an unread failure with the state. For a loop that exchanges data with the host every step
+   (set vertices, step, read vertices) this leaves one synchronisation per step.
+   IBLB_EINVAL for nsteps < 0. */
+int iblb_step_async(iblb_ctx *ctx, int32_t nsteps);
+
+/* Read the health word of steps queued by iblb_step_async (synchronises); IBLB_OK if there
+   are none or they passed, else the failure as iblb_step reports it. */
+int iblb_check_health(iblb_ctx *ctx);
+
 /* rho [nz][ny][nx] and u [nz][ny][nx][3] of the current post-streaming state; u carries half
    of the force of the last spreading step (none before the first step) plus the body force.
    Wall-layer nodes report rho0 and their wall velocity. */

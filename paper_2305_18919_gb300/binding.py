@@ -70,6 +70,8 @@ SIGNATURES = {
     "iblb_set_vertices": (_i32, [_vp, _i32, _dp]),
     "iblb_init_equilibrium": (_i32, [_vp, _dp, _dp]),
     "iblb_step": (_i32, [_vp, _i32]),
+    "iblb_step_async": (_i32, [_vp, _i32]),
+    "iblb_check_health": (_i32, [_vp]),
     "iblb_read_fields": (_i32, [_vp, _dp, _dp]),
     "iblb_read_fields_device": (_i32, [_vp, _vp, _vp]),
     "iblb_read_populations": (_i32, [_vp, _dp]),
@@ -263,6 +265,14 @@ class Lattice:
     # --- stepping ------------------------------------------------------------------
     def step(self, n=1):
         self._check(self._L.iblb_step(self.h, int(n)))
+
+    def step_async(self, n=1):
+        """Queue n steps without reading the health word (iblb_step_async); a failure is raised
+        by the next read-back or check_health()."""
+        self._check(self._L.iblb_step_async(self.h, int(n)))
+
+    def check_health(self):
+        self._check(self._L.iblb_check_health(self.h))
 
     @property
     def steps_done(self) -> int:

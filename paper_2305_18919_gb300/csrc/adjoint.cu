@@ -830,6 +830,7 @@ int iblb_adjoint_record(iblb_ctx *h, int32_t nsteps, int32_t every) {
     return iblb::afail(c, IBLB_EINVAL, "the adjoint needs an IBLB_FP64 or IBLB_FP32 context");
   if (c.nv == 0) return iblb::afail(c, IBLB_EINVAL, "no mesh has been added");
   if (nsteps < 1 || every < 1) return iblb::afail(c, IBLB_EINVAL, "nsteps and every must be >= 1");
+  if (int rc = iblb::settle_health(c)) return rc;  // a failure of earlier iblb_step_async steps
   iblb::adjoint_free(c);
   auto *a = new iblb::Adjoint();
   c.adj = a;
@@ -864,6 +865,7 @@ int iblb_adjoint_gradient(iblb_ctx *h, const double *dJdq, double *dJdtheta) {
   Ctx &c = h->c;
   auto *a = (iblb::Adjoint *)c.adj;
   if (!a) return iblb::afail(c, IBLB_EINVAL, "no trajectory recorded (iblb_adjoint_record)");
+  if (int rc = iblb::settle_health(c)) return rc;
   const size_t pn = (size_t)iblb::Q * c.ncell, qn = (size_t)3 * c.nv;
   // work arrays (kept for later calls)
   if (!a->lam_q) {

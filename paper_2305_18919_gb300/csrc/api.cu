@@ -326,6 +326,7 @@ int iblb_create(const iblb_lattice_desc *d, void *cuda_stream, iblb_ctx **out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_coll, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_sync, cudaEventDisableTiming);
   if (e == cudaSuccess) e = dalloc(&c.counters, 8);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&c.health_host, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(c.counters, 0, 8 * sizeof(int), c.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
   if (e != cudaSuccess) {
@@ -353,6 +354,7 @@ void iblb_destroy(iblb_ctx *h) {
   dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.xref); dfree(c.fgeo); dfree(c.disp); dfree(c.vf_start); dfree(c.vf_list);
   dfree(c.fcontrib); dfree(c.fnorm); dfree(c.vol_partial); dfree(c.phi); dfree(c.gvol); dfree(c.stencil);
   dfree(c.dscratch);
+  if (c.health_host) cudaFreeHost(c.health_host);
   iblb::adjoint_free(c);
   for (cudaEvent_t ev : c.ev_pool) cudaEventDestroy(ev);
   for (cudaEvent_t ev : c.ev_near) cudaEventDestroy(ev);
@@ -507,6 +509,7 @@ int iblb_init_equilibrium(iblb_ctx *h, const double *rho, const double *u) {
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
   c.fresh = 1;
   c.have_force = 0;
+  c.health_pending = 0;  // the state those steps left is gone
   c.config_gen++;
   return IBLB_OK;
 }
@@ -522,6 +525,7 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
   Ctx &c = h->c;
   if (nsteps < 0) return fail(c, IBLB_EINVAL, "nsteps < 0");
   if (nsteps == 0) return IBLB_OK;
+  if (int rc = iblb::settle_health(c)) return rc;  // a failure of earlier iblb_step_async steps
   CUDA_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
   // the health word is read every health_every steps (and at the end), so that a run that goes
   // unstable stops near where it did
@@ -535,6 +539,23 @@ int iblb_step(iblb_ctx *h, int32_t nsteps) {
     if (hw) return health_error(c, hw);
   }
   return IBLB_OK;
+}
+
+int iblb_step_async(iblb_ctx *h, int32_t nsteps) {
+  if (!h) return IBLB_EINVAL;
+  Ctx &c = h->c;
+  if (nsteps < 0) return fail(c, IBLB_EINVAL, "nsteps < 0");
+  if (nsteps == 0) return IBLB_OK;
+  // a failure still unread stays in the health word; otherwise it starts clear
+  if (!c.health_pending) CUDA_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
+  if (int rc = iblb::enqueue_steps(c, nsteps)) return rc;
+  c.health_pending = 1;
+  return IBLB_OK;
+}
+
+int iblb_check_health(iblb_ctx *h) {
+  if (!h) return IBLB_EINVAL;
+  return iblb::settle_health(h->c);
 }
 
 int iblb_set_health_interval(iblb_ctx *h, int32_t every) {
@@ -612,6 +633,27 @@ int enqueue_steps(Ctx &c, int nsteps) {
 
 int health_status(Ctx &c, int hw) { return hw ? health_error(c, hw) : IBLB_OK; }
 
+int settle_health(Ctx &c) {
+  if (!c.health_pending) return IBLB_OK;
+  c.health_pending = 0;
+  int hw = 0;
+  if (int rc = read_health(c, &hw)) return rc;
+  return health_status(c, hw);
+}
+
+int queue_health(Ctx &c) {
+  if (c.health_pending)
+    CUDA_TRY(c, cudaMemcpyAsync(c.health_host, c.counters + 3, sizeof(int), cudaMemcpyDeviceToHost,
+                                c.stream));
+  return IBLB_OK;
+}
+
+int pending_health(Ctx &c) {
+  if (!c.health_pending) return IBLB_OK;
+  c.health_pending = 0;
+  return health_status(c, *c.health_host);
+}
+
 int restore_state(Ctx &c, const void *P, const double *q, int fresh) {
   CUDA_TRY(c, cudaMemcpyAsync(c.f[c.cur], P, (size_t)Q * c.ncell * c.pop_size,
                               cudaMemcpyDeviceToDevice, c.stream));
@@ -629,11 +671,12 @@ int iblb_read_fields(iblb_ctx *h, double *rho, double *u) {
   if (!h || !rho || !u) return IBLB_EINVAL;
   Ctx &c = h->c;
   if (int rc = staging(c, 4 * c.ncell)) return rc;
+  if (int rc = iblb::queue_health(c)) return rc;
   CUDA_TRY(c, iblb::launch_fields(c, c.dscratch, c.dscratch + c.ncell));
   CUDA_TRY(c, cudaMemcpyAsync(rho, c.dscratch, c.ncell * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CUDA_TRY(c, cudaMemcpyAsync(u, c.dscratch + c.ncell, 3 * c.ncell * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
-  return IBLB_OK;
+  return iblb::pending_health(c);
 }
 
 int iblb_read_fields_device(iblb_ctx *h, double *rho_dev, double *u_dev) {
@@ -657,9 +700,10 @@ int iblb_read_vertices(iblb_ctx *h, int32_t mesh_id, double *q) {
   if (!h || !q) return IBLB_EINVAL;
   Ctx &c = h->c;
   if (int rc = check_mesh_id(c, mesh_id)) return rc;
+  if (int rc = iblb::queue_health(c)) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(q, c.q, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
-  return IBLB_OK;
+  return iblb::pending_health(c);
 }
 
 int iblb_read_vertices_device(iblb_ctx *h, int32_t mesh_id, double *q_dev) {
@@ -674,9 +718,10 @@ int iblb_read_vertex_velocities(iblb_ctx *h, int32_t mesh_id, double *qdot) {
   if (!h || !qdot) return IBLB_EINVAL;
   Ctx &c = h->c;
   if (int rc = check_mesh_id(c, mesh_id)) return rc;
+  if (int rc = iblb::queue_health(c)) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(qdot, c.qdot, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
-  return IBLB_OK;
+  return iblb::pending_health(c);
 }
 
 int iblb_read_forces(iblb_ctx *h, int32_t mesh_id, double *phi) {
@@ -684,18 +729,20 @@ int iblb_read_forces(iblb_ctx *h, int32_t mesh_id, double *phi) {
   Ctx &c = h->c;
   if (int rc = check_mesh_id(c, mesh_id)) return rc;
   if (int rc = staging(c, (size_t)3 * c.nv)) return rc;
+  if (int rc = iblb::queue_health(c)) return rc;
   CUDA_TRY(c, iblb::launch_face_forces(c, 0, c.stream));
   CUDA_TRY(c, iblb::launch_vertex_forces(c, 0, c.stream));
   CUDA_TRY(c, iblb::launch_phi_to_double(c, c.dscratch));
   CUDA_TRY(c, cudaMemcpyAsync(phi, c.dscratch, (size_t)3 * c.nv * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
-  return IBLB_OK;
+  return iblb::pending_health(c);
 }
 
 int iblb_read_force_field(iblb_ctx *h, double *F) {
   if (!h || !F) return IBLB_EINVAL;
   Ctx &c = h->c;
   if (int rc = staging(c, 3 * c.ncell)) return rc;
+  if (int rc = iblb::settle_health(c)) return rc;  // the health word is reused below
   CUDA_TRY(c, cudaMemsetAsync(c.dscratch, 0, 3 * c.ncell * sizeof(double), c.stream));
   if (c.nv) {
     CUDA_TRY(c, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
@@ -720,12 +767,13 @@ int iblb_read_volume(iblb_ctx *h, int32_t mesh_id, double *V, double *V0) {
   Ctx &c = h->c;
   if (int rc = check_mesh_id(c, mesh_id)) return rc;
   if (int rc = staging(c, 1)) return rc;
+  if (int rc = iblb::queue_health(c)) return rc;
   CUDA_TRY(c, iblb::launch_face_forces(c, 0, c.stream));
   CUDA_TRY(c, iblb::launch_volume(c, c.dscratch));
   CUDA_TRY(c, cudaMemcpyAsync(V, c.dscratch, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CUDA_TRY(c, cudaStreamSynchronize(c.stream));
   *V0 = c.V0;
-  return IBLB_OK;
+  return iblb::pending_health(c);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -816,6 +864,7 @@ int iblb_load_state(iblb_ctx *h, const char *path) {
   for (int k = 0; k < 3; k++) { c.ub[k] = hd.ub[k]; c.ut[k] = hd.ut[k]; c.g[k] = hd.g[k]; }
   c.fresh = hd.fresh;
   c.steps_done = hd.steps_done;
+  c.health_pending = 0;  // the state of any unread iblb_step_async steps is replaced
   CUDA_TRY(c, cudaMemcpyAsync(c.f[c.cur], fbuf.data(), fbytes, cudaMemcpyHostToDevice, c.stream));
   if (c.nv) {
     std::vector<double> fref, fgeo;

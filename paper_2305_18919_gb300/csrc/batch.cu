@@ -375,7 +375,8 @@ int iblb_batch_step(iblb_batch *b, int32_t nsteps) {
   for (size_t i = 0; i < n; i++) {
     Ctx &c = b->inst[i]->c;
     BATCH_TRY(b, follow(c.stream, b->stream, b->joins[i]));
-    BATCH_TRY(b, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
+    // a failure of the instance's own iblb_step_async steps, still unread, stays in the word
+    if (!c.health_pending) BATCH_TRY(b, cudaMemsetAsync(c.counters + 3, 0, sizeof(int), c.stream));
   }
   int done = 0;
   // a freshly initialised state is collided in place by its first step, which the batched
@@ -421,6 +422,7 @@ int iblb_batch_step(iblb_batch *b, int32_t nsteps) {
   BATCH_TRY(b, cudaStreamSynchronize(b->stream));
   int first = IBLB_OK;
   for (size_t i = 0; i < n; i++) {
+    b->inst[i]->c.health_pending = 0;
     b->status[i] = iblb::health_status(b->inst[i]->c, b->health[i]);
     if (b->status[i] != IBLB_OK && first == IBLB_OK) {
       first = b->status[i];

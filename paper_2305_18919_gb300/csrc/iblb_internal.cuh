@@ -183,6 +183,8 @@ struct Ctx {
   unsigned long long stage_wait_ns = 1000000000ull;  // limit of a staged pass's waits (ns)
   int smem_optin = 0;       // shared memory a block may opt in to (bytes)
   int health_every = 1000;  // iblb_step reads the health word every this many steps (0: at its end)
+  int health_pending = 0;   // steps queued by iblb_step_async whose health word is unread
+  int *health_host = nullptr;  // pinned: the health word read with a call's own transfers
   uint64_t config_gen = 0;  // bumped by every call that changes what a queued step launches
   std::string err;
 };
@@ -202,6 +204,12 @@ int health_status(Ctx &c, int health_word);
 // arrays), with the given fresh flag, and mark the tiles of q: the next step continues from
 // there exactly as from the state that P and q were copied from.
 int restore_state(Ctx &c, const void *P, const double *q, int fresh);
+// A failure of steps queued by iblb_step_async: read with a synchronisation (settle_health), or
+// queued before a read call's own synchronisation (queue_health) and taken after it
+// (pending_health). Each returns IBLB_OK or the failure, and clears the pending mark.
+int settle_health(Ctx &c);
+int queue_health(Ctx &c);
+int pending_health(Ctx &c);
 // Release the adjoint's memory (no-op without one).
 void adjoint_free(Ctx &c);
 // Lattice rows per block of the stream-collide pass (k1_rows within the launch bound).

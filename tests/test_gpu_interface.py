@@ -160,6 +160,68 @@ def test_save_load_roundtrip(tmp_path):
     np.testing.assert_array_equal(a.populations(), b.populations())
 
 
+def _gpu_only(wl):
+    from paper_2305_18919_gb300 import binding
+    lat = binding.Lattice(wl.nx, wl.ny, wl.nz, wl.tau, 1.0, wl.wall_u_bottom, wl.wall_u_top,
+                          wl.body_force, "fp32")
+    v, f = wl.mesh()
+    lat.add_mesh(v, f)
+    lat.set_interface(wl.alpha, wl.kV, wl.eps, wl.xi, wl.wall_force_on, wl.volume_force_on)
+    return lat
+
+
+def test_step_async_matches_step():
+    """iblb_step_async queues the steps of iblb_step (same kernels, same order) without reading
+    the health word: the host-exchange loop of the end-to-end benchmark gives the same vertices
+    and populations, bit for bit, either way."""
+    wl = _wetting(precision="fp32")
+    a, b = _gpu_only(wl), _gpu_only(wl)
+    qa, qb = a.vertices(), b.vertices()
+    for _ in range(6):
+        a.set_vertices(qa)
+        a.step(1)
+        qa = a.vertices()
+        b.set_vertices(qb)
+        b.step_async(1)
+        qb = b.vertices()
+    np.testing.assert_array_equal(qa, qb)
+    b.step_async(3)
+    a.step(3)
+    b.check_health()
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    assert a.steps_done == b.steps_done == 9
+    a.close()
+    b.close()
+
+
+def test_step_async_failure_is_reported_by_the_next_read():
+    """A failed health check of iblb_step_async steps comes back from the next call that reads
+    the health word (here the vertex read-back, then iblb_step), once."""
+    from paper_2305_18919_gb300 import binding
+    wl = _wetting(precision="fp32")
+    v, _ = wl.mesh()
+    lat = _gpu_only(wl)
+    lat.set_vertices(wl.centre + (v - wl.centre) * 0.9)  # |V/V0 - 1| past 5 %
+    lat.step_async(2)  # queued: no error yet
+    lat.step_async(1)  # the first failure is kept
+    with pytest.raises(binding.IBLBError) as e:
+        lat.vertices()
+    assert e.value.code == binding.IBLB_EUNSTABLE
+    lat.vertices()  # read once: the next read is clean
+    lat.check_health()
+    lat.step_async(1)
+    done = lat.steps_done
+    with pytest.raises(binding.IBLBError) as e:
+        lat.step(5)  # reports the queued failure before running anything
+    assert e.value.code == binding.IBLB_EUNSTABLE
+    assert lat.steps_done == done
+    lat.step_async(1)
+    with pytest.raises(binding.IBLBError) as e:
+        lat.check_health()
+    assert e.value.code == binding.IBLB_EUNSTABLE
+    lat.close()
+
+
 def test_errors_are_reported():
     from paper_2305_18919_gb300 import binding
     wl = _wetting(precision="fp32")
