@@ -503,7 +503,8 @@ def run_gpu(args, wl, rank, world):
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if wl.precision == "fp64" else "f32",
-        "data": "synthetic", "config": dict(config_of(wl), interface_sms=ib_sms),
+        "data": "synthetic", "config": config_of(wl),
+        "interface_sms": ib_sms,  # the SM partition (a launch setting, not part of the workload)
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "h2d_bytes_per_step": nv * 24,

@@ -309,15 +309,16 @@ int iblb_create(const iblb_lattice_desc *d, void *cuda_stream, iblb_ctx **out) {
   int prio_lo = 0, prio_hi = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   // Default split, from sweeps of the interface SMs. A full-lattice pass of at least 1 GiB
-  // hides the interface chain on 32 SMs (256^3 FP32, 2.5 GB: 39.5k MLUPS against 34.8k
-  // unpartitioned); 16-bit storage halves the pass, so the chain takes 40 (256^3 FP16: 64.9k
-  // against 55.8k on 32 SMs). A shorter pass leaves the chain as the critical path, which then
-  // takes 64 SMs (128x128x96 FP32 wetting, 1.5 M nodes: 0.090 ms against 0.115 ms on 32 SMs;
-  // 32^3 FP64 shear: 0.136 ms against 0.138 ms on 32 and 0.149 ms unpartitioned).
+  // hides the interface chain on 24 SMs (256^3 FP32, 2.5 GB: 40.3k MLUPS against 39.3k on 32,
+  // 31.5k on 16 and 34.8k unpartitioned); 16-bit storage halves the pass, so the chain takes
+  // 40 (256^3 FP16: 66.0k against 59.0k on 32). A shorter pass leaves the chain as the
+  // critical path, which then takes 64 SMs (128x128x96 FP32 wetting, 1.5 M nodes: 0.090 ms
+  // against 0.115 ms on 32 SMs; 32^3 FP64 shear: 0.136 ms against 0.138 ms on 32 and
+  // 0.149 ms unpartitioned).
   const size_t pass_bytes = (size_t)2 * iblb::Q * c.ncell * c.pop_size;
   const int want = d->ib_sms != 0 ? d->ib_sms
                    : pass_bytes < ((size_t)1 << 30) ? 64
-                   : (c.pop_size == 2 ? 40 : 32);
+                   : (c.pop_size == 2 ? 40 : 24);
   if (e == cudaSuccess && !(want > 0 && make_partitions(c, want, prio_hi))) {
     e = cudaStreamCreateWithPriority(&c.ib, cudaStreamNonBlocking, prio_hi);
     c.ls = c.stream;
