@@ -198,7 +198,7 @@ bool reference_shape(const double *verts, int nv, const int32_t *faces, int nf, 
                      double zt, std::vector<double> &fref, std::vector<double> &fgeo,
                      double centre[3], double *V0_out) {
   fref.assign((size_t)4 * nf, 0.0);
-  fgeo.assign((size_t)12 * nf, 0.0);
+  fgeo.assign((size_t)16 * nf, 0.0);
   for (int k = 0; k < 3; k++) centre[k] = 0.0;
   for (int i = 0; i < nv; i++)
     for (int k = 0; k < 3; k++) centre[k] += verts[3 * i + k] / nv;
@@ -224,13 +224,14 @@ bool reference_shape(const double *verts, int nv, const int32_t *faces, int nf, 
     fref[4 * j + 2] = g11 / det;
     fref[4 * j + 3] = 0.5 * std::sqrt(det);
     for (int k = 0; k < 3; k++) {
-      fgeo[12 * j + k] = a[k];
-      fgeo[12 * j + 3 + k] = b[k];
-      fgeo[12 * j + 6 + k] = r0[k];
+      fgeo[16 * j + k] = a[k];
+      fgeo[16 * j + 3 + k] = b[k];
+      fgeo[16 * j + 6 + k] = r0[k];
     }
     const double gz = (X0[2] + X1[2] + X2[2]) / 3.0;
-    fgeo[12 * j + 9] = gz - zb;
-    fgeo[12 * j + 10] = gz - zt;
+    fgeo[16 * j + 9] = gz - zb;
+    fgeo[16 * j + 10] = gz - zt;
+    for (int k = 0; k < 4; k++) fgeo[16 * j + 12 + k] = fref[4 * j + k];  // in the face kernel's type
     V0 += (r0[0] * (r1[1] * r2[2] - r1[2] * r2[1]) + r0[1] * (r1[2] * r2[0] - r1[0] * r2[2]) +
            r0[2] * (r1[0] * r2[1] - r1[1] * r2[0])) / 6.0;
   }
@@ -249,11 +250,16 @@ int upload_reference(Ctx &c, const double *X, const std::vector<double> &fref,
   c.tile_estimate = (int)(est < c.max_slots ? est : c.max_slots);
   CUDA_TRY(c, cudaMemcpyAsync(c.fref, fref.data(), fref.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   CUDA_TRY(c, cudaMemcpyAsync(c.xref, X, (size_t)3 * c.nv * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  // the face kernel reads the per-face data by component: [16][nf]
+  const size_t nf = fgeo.size() / 16;
+  std::vector<double> soa(fgeo.size());
+  for (size_t j = 0; j < nf; j++)
+    for (size_t k = 0; k < 16; k++) soa[k * nf + j] = fgeo[16 * j + k];
   if (c.precision == IBLB_FP64) {
-    CUDA_TRY(c, cudaMemcpyAsync(c.fgeo, fgeo.data(), fgeo.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c.fgeo, soa.data(), soa.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
     CUDA_TRY(c, cudaStreamSynchronize(c.stream));  // the host buffers are the caller's locals
   } else {
-    std::vector<float> g32(fgeo.begin(), fgeo.end());
+    std::vector<float> g32(soa.begin(), soa.end());
     CUDA_TRY(c, cudaMemcpyAsync(c.fgeo, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice, c.stream));
     CUDA_TRY(c, cudaStreamSynchronize(c.stream));
   }
@@ -352,7 +358,7 @@ void iblb_destroy(iblb_ctx *h) {
     dfree(c.Fslot[b]);
   }
   dfree(c.counters); dfree(c.slot_count); dfree(c.src_index); dfree(c.Rslot); dfree(c.bucket); dfree(c.spill_bits); dfree(c.Uslot); dfree(c.pair_list);
-  dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.xref); dfree(c.fgeo); dfree(c.disp); dfree(c.vf_start); dfree(c.vf_list);
+  dfree(c.q); dfree(c.qdot); dfree(c.faces); dfree(c.fref); dfree(c.xref); dfree(c.fgeo); dfree(c.vcoef); dfree(c.disp); dfree(c.vf_start); dfree(c.vf_list);
   dfree(c.fcontrib); dfree(c.fnorm); dfree(c.vol_partial); dfree(c.phi); dfree(c.gvol); dfree(c.stencil);
   dfree(c.dscratch);
   if (c.health_host) cudaFreeHost(c.health_host);
@@ -432,7 +438,8 @@ int iblb_add_mesh(iblb_ctx *h, const double *verts, int32_t nv, const int32_t *f
   CUDA_TRY(c, dalloc(&c.faces, (size_t)3 * nf));
   CUDA_TRY(c, dalloc(&c.fref, (size_t)4 * nf));
   CUDA_TRY(c, dalloc(&c.xref, (size_t)3 * nv));
-  CUDA_TRY(c, dalloc_bytes(&c.fgeo, (size_t)12 * nf * rs));
+  CUDA_TRY(c, dalloc_bytes(&c.fgeo, (size_t)16 * nf * rs));
+  CUDA_TRY(c, dalloc_bytes(&c.vcoef, sizeof(double)));
   CUDA_TRY(c, dalloc_bytes(&c.disp, (size_t)4 * nv * rs));
   CUDA_TRY(c, dalloc(&c.vf_start, (size_t)nv + 1));
   CUDA_TRY(c, dalloc(&c.vf_list, (size_t)3 * nf));

@@ -54,13 +54,19 @@ __device__ __forceinline__ real lj_fz(real dz, real eps48, real xi) {
   return eps48 * (s6 * s6 - real(0.5) * s6) * dz * inv_d2;
 }
 
-// Per-face reference data in the population type: A, B (edges), X0 - c, and the reference
-// centroid height above the bottom and the top wall plane; padded to 12.
-constexpr int FGEO = 12;
+// Per-face reference data in the population type, stored by component ([FGEO][nf]): A, B
+// (edges), X0 - c, the reference centroid height above the bottom and the top wall plane, a
+// pad, and the reference metric inverse H11, H12, H22 with the reference area A0 (rounded
+// once on the host).
+constexpr int FGEO = 16;
 
+// Interface parameters of the face kernel, rounded once to the population type on the host
+// (FP64 issues at 1/64 of the FP32 rate on this GPU: no per-face conversions).
+template <typename real>
 struct FaceParams {
-  double a1, a2, a3;  // alpha
-  double eps48, xi;
+  real a3;        // alpha3
+  real cL0, cL1;  // 0.5 (alpha1 - alpha3), 0.25 (alpha1 + alpha2)
+  real eps48, xi;
   int wall_on;
 };
 
@@ -80,11 +86,10 @@ struct FaceArgs {
   int nf;
   const int *faces;
   const Vec4<real> *disp;
-  const double *fref;
   const real *fgeo;
   real *fcontrib, *fnorm;
   double *vol_partial;
-  FaceParams fp;
+  FaceParams<real> fp;
   Dims D;
   int *other_tile_slot;
   const int *other_slot_tile, *other_nslots;
@@ -100,12 +105,11 @@ __device__ __forceinline__ void face_body(const FaceArgs<real> &A, int bid, int 
   const int nf = A.nf;
   const int *__restrict__ faces = A.faces;
   const Vec4<real> *__restrict__ disp = A.disp;
-  const double *__restrict__ fref = A.fref;
   const real *__restrict__ fgeo = A.fgeo;
   real *__restrict__ fcontrib = A.fcontrib;
   real *__restrict__ fnorm = A.fnorm;
   double *__restrict__ vol_partial = A.vol_partial;
-  const FaceParams fp = A.fp;
+  const FaceParams<real> fp = A.fp;
   const Dims D = A.D;
   __shared__ double warp_sum[8];
   const int j = bid * blockDim.x + threadIdx.x;
@@ -119,7 +123,11 @@ __device__ __forceinline__ void face_body(const FaceArgs<real> &A, int bid, int 
       u[c][1] = d.y;
       u[c][2] = d.z;
     }
-    const real *geo = fgeo + FGEO * (size_t)j;  // A, B, X0 - c, centroid heights above walls
+    // A, B, X0 - c, centroid heights above the walls, pad, H11 H12 H22 A0; stored by
+    // component ([FGEO][nf]), so that each load of a warp reads one contiguous row
+    real geo[FGEO];
+#pragma unroll
+    for (int k = 0; k < FGEO; k++) geo[k] = k == 11 ? real(0) : fgeo[(size_t)k * nf + j];
     real A[3], B[3], X0c[3], da[3], db[3], a[3], b[3];
     for (int k = 0; k < 3; k++) {
       A[k] = geo[k];
@@ -130,15 +138,14 @@ __device__ __forceinline__ void face_body(const FaceArgs<real> &A, int bid, int 
       a[k] = A[k] + da[k];
       b[k] = B[k] + db[k];
     }
-    const real H11 = (real)fref[4 * j], H12 = (real)fref[4 * j + 1], H22 = (real)fref[4 * j + 2],
-               A0 = (real)fref[4 * j + 3];
+    const real H11 = geo[12], H12 = geo[13], H22 = geo[14], A0 = geo[15];
     const real G11 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
     const real G12 = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
     const real G22 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
     const real detG = G11 * G22 - G12 * G12;
     const real L = log_(detG / (real(4) * A0 * A0));  // log(I2 + 1), det G0 = 4 A0^2
-    const real dE_dI1 = real(0.5) * (real)fp.a3 * A0;
-    const real dE_dL = A0 * ((real)(0.5 * (fp.a1 - fp.a3)) + (real)(0.25 * (fp.a1 + fp.a2)) * L);
+    const real dE_dI1 = real(0.5) * fp.a3 * A0;
+    const real dE_dL = A0 * (fp.cL0 + fp.cL1 * L);
     const real inv_detG = real(1) / detG;
     real f0[3], f1[3], f2[3];
     for (int k = 0; k < 3; k++) {
@@ -155,8 +162,8 @@ __device__ __forceinline__ void face_body(const FaceArgs<real> &A, int bid, int 
       // centroid height above each wall plane: reference height (from the set-up, in double)
       // plus the mean displacement
       const real uz = (u[0][2] + u[1][2] + u[2][2]) * real(1.0 / 3.0);
-      const real third = (lj_fz<real>(geo[9] + uz, (real)fp.eps48, (real)fp.xi) +
-                          lj_fz<real>(geo[10] + uz, (real)fp.eps48, (real)fp.xi)) *
+      const real third = (lj_fz<real>(geo[9] + uz, fp.eps48, fp.xi) +
+                          lj_fz<real>(geo[10] + uz, fp.eps48, fp.xi)) *
                          real(1.0 / 3.0);
       f0[2] += third;
       f1[2] += third;
@@ -255,6 +262,11 @@ constexpr int GATHER_UNROLL = 8;
 // volume term -kV (V - V0)/V0 g is added where the force is used (spreading, read-back),
 // after V is complete. Then the delta stencil of the vertex and its binning into the source
 // tile (the tile that holds its base node).
+struct VolumeParams {
+  double V0, kV;
+  int volume_on, vol_blocks;
+};
+
 template <typename real>
 struct VertexArgs {
   int nv;
@@ -267,6 +279,9 @@ struct VertexArgs {
   const int *tile_slot;
   int *slot_count, *bucket, *ovf_count, *src_index, *nsources, *health, *zero_counter;
   unsigned *spill_bits;  // bit i: vertex i did not fit in its tile's bucket
+  const double *vol_partial;  // per-block V_j - V0_j partials of the face kernel
+  VolumeParams vp;
+  real *vcoef;                // out: kV (V - V0)/V0 for the spreading pass
   Dims D;
 };
 
@@ -282,6 +297,17 @@ __device__ __forceinline__ void vertex_body(const VertexArgs<real> &A, int bid) 
   const Dims D = A.D;
   const int i = bid * blockDim.x + threadIdx.x;
   if (bid == 0 && threadIdx.x == 0 && A.zero_counter) *A.zero_counter = 0;
+  if (bid == 0 && threadIdx.x < 32) {
+    // the volume-force coefficient of the step, once (the spreading pass reads it), and the
+    // volume health check
+    double V;
+    const real coef = (real)volume_coef(A.vol_partial, A.vp.vol_blocks, A.vp.V0, A.vp.kV,
+                                        A.vp.volume_on, &V);
+    if (threadIdx.x == 0) {
+      *A.vcoef = coef;
+      if (!(fabs(V / A.vp.V0 - 1.0) <= 0.05)) atomicOr(A.health, H_VOLUME);
+    }
+  }
   if (i >= nv) return;
   const int e0 = vf_start[i], e1 = vf_start[i + 1];
   real F[3] = {0, 0, 0}, g[3] = {0, 0, 0};
@@ -348,11 +374,6 @@ __global__ void __launch_bounds__(256) vertex_kernel_multi(
   vertex_body(all[m.inst], m.block);
 }
 
-struct VolumeParams {
-  double V0, kV;
-  int volume_on, vol_blocks;
-};
-
 // Spreading works on regions: the stencils of the vertices binned in a source tile S (base
 // node in S) cover the 7x7x7 nodes S_lo .. S_lo + 6.
 constexpr int REGION = 7;
@@ -386,9 +407,7 @@ struct SourceArgs {
   int spill_words;
   const StencilRec<real> *stencil;
   const Vec4<real> *phi, *gvol;
-  const double *vol_partial;
-  VolumeParams vp;
-  int *health;
+  const real *vcoef;  // kV (V - V0)/V0, written by the vertex kernel of the step
   Vec4<real> *Rslot;
   int *out_src;
   Dims D;
@@ -405,7 +424,6 @@ __device__ __forceinline__ void spread_source_body(const SourceArgs<real> &A, in
   const StencilRec<real> *__restrict__ stencil = A.stencil;
   const Vec4<real> *__restrict__ phi = A.phi;
   const Vec4<real> *__restrict__ gvol = A.gvol;
-  const VolumeParams vp = A.vp;
   int *__restrict__ out_src = A.out_src;
   const Dims D = A.D;
   constexpr int W = SrcWarps<real>::value;
@@ -415,10 +433,7 @@ __device__ __forceinline__ void spread_source_body(const SourceArgs<real> &A, in
   __shared__ int s_b[W][BUCKET_CAP][3];
   const int nslots = min(*A.nslots_ptr, D.max_slots);
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  double V;
-  const real coef = (real)volume_coef(A.vol_partial, vp.vol_blocks, vp.V0, vp.kV, vp.volume_on, &V);
-  if (bid == 0 && threadIdx.x == 0 && !(fabs(V / vp.V0 - 1.0) <= 0.05))
-    atomicOr(A.health, H_VOLUME);
+  const real coef = *A.vcoef;
   Vec4<real> *region = s_region[wq];
   // the two stencil nodes of this lane
   const int dxa = lane & 3, dya = (lane >> 2) & 3, dza = lane >> 4;  // node lane; node lane + 32
@@ -698,8 +713,8 @@ __device__ __forceinline__ void mark_tile(const AxisTiles ax[3], int e, const Di
 
 // K2: interpolation (Eq. 11) and the Euler update (Eq. 12); 4 lanes per vertex, lane dz
 // sums the 16 nodes of its z-plane of the stencil, the 4 planes are summed by shuffles and
-// the update is added to the double position. Each lane then marks two of the (up to 8)
-// tiles of the new position in the other map.
+// the update is added to the double position by lane 0, which also finds the tiles of the new
+// stencil; each lane then marks two of those (up to 8) tiles in the other map.
 // The delta-weight accumulation of a vertex is carried at double precision in every
 // precision (VertexSum): each stencil row's four products w_x u (one x row of a tile, in the
 // arithmetic type) is added to the vertex's sum with its weight w_y w_z, and the four planes'
@@ -844,38 +859,55 @@ __device__ __forceinline__ void interp_body(const InterpArgs<real> &A, int bid) 
   }
   // sum of the 4 planes (fixed butterfly order)
   for (int o = 2; o > 0; o >>= 1) acc.add_lanes(o);
-  if (valid) {
+  // lane dz == 0 updates the vertex in double and finds the tiles of its new stencil; the
+  // other three lanes take the tiles from it (FP64 issues at 1/64 of the FP32 rate on this
+  // GPU, so that work is done once per vertex)
+  int tq[6] = {0, 0, 0, 0, 0, 0};  // t0, t1 of each axis
+  int flags = 0;                   // bit 2k / 2k + 1: ok0 / ok1 of axis k; bit 6: mark
+  if (valid && dz == 0) {
     double pn[3], qd[3];
+    int h = 0;
     for (int k = 0; k < 3; k++) {
       qd[k] = acc.value(k);
       pn[k] = q[3 * (size_t)v + k] + qd[k];
+      qdot[3 * (size_t)v + k] = qd[k];
+      q[3 * (size_t)v + k] = pn[k];
+      if (!(fabs(qd[k]) < 0.1)) h |= (qd[k] == qd[k]) ? H_FAST : H_NAN;
     }
-    if (dz == 0) {
-      int h = 0;
-      for (int k = 0; k < 3; k++) {
-        qdot[3 * (size_t)v + k] = qd[k];
-        q[3 * (size_t)v + k] = pn[k];
-        if (!(fabs(qd[k]) < 0.1)) h |= (qd[k] == qd[k]) ? H_FAST : H_NAN;
-      }
-      if (D.has_walls && (pn[2] - D.zb < 0.05 || D.zt - pn[2] < 0.05)) h |= H_WALL;
-      if (h) atomicOr(health, h);
-      Vec4<real> d;
-      d.x = (real)(pn[0] - xref[3 * (size_t)v]);
-      d.y = (real)(pn[1] - xref[3 * (size_t)v + 1]);
-      d.z = (real)(pn[2] - xref[3 * (size_t)v + 2]);
-      d.w = real(0);
-      disp[v] = d;
-    }
+    if (D.has_walls && (pn[2] - D.zb < 0.05 || D.zt - pn[2] < 0.05)) h |= H_WALL;
+    if (h) atomicOr(health, h);
+    Vec4<real> d;
+    d.x = (real)(pn[0] - xref[3 * (size_t)v]);
+    d.y = (real)(pn[1] - xref[3 * (size_t)v + 1]);
+    d.z = (real)(pn[2] - xref[3 * (size_t)v + 2]);
+    d.w = real(0);
+    disp[v] = d;
     if (next_tile_slot != nullptr && pn[0] == pn[0] && pn[1] == pn[1] && pn[2] == pn[2]) {
-      AxisTiles ax[3];
-      ax[0] = axis_tiles(pn[0], D.ntx, D.inx, true);
-      ax[1] = axis_tiles(pn[1], D.nty, D.iny, true);
-      ax[2] = axis_tiles(pn[2], D.ntz, D.inz, !D.has_walls);
-      mark_tile(ax, dz, D, next_tile_slot, A.next_slot_tile, A.next_nslots, A.slot_count,
-                A.out_src, health);
-      mark_tile(ax, dz + 4, D, next_tile_slot, A.next_slot_tile, A.next_nslots, A.slot_count,
-                A.out_src, health);
+      const AxisTiles ax[3] = {axis_tiles(pn[0], D.ntx, D.inx, true),
+                               axis_tiles(pn[1], D.nty, D.iny, true),
+                               axis_tiles(pn[2], D.ntz, D.inz, !D.has_walls)};
+      for (int k = 0; k < 3; k++) {
+        tq[2 * k] = ax[k].t0;
+        tq[2 * k + 1] = ax[k].t1;
+        flags |= (ax[k].ok0 ? 1 : 0) << (2 * k) | (ax[k].ok1 ? 1 : 0) << (2 * k + 1);
+      }
+      flags |= 64;
     }
+  }
+  for (int k = 0; k < 6; k++) tq[k] = __shfl_sync(0xffffffffu, tq[k], 0, 4);
+  flags = __shfl_sync(0xffffffffu, flags, 0, 4);
+  if (valid && (flags & 64)) {  // each lane claims two of the (up to 8) tiles
+    AxisTiles ax[3];
+    for (int k = 0; k < 3; k++) {
+      ax[k].t0 = tq[2 * k];
+      ax[k].t1 = tq[2 * k + 1];
+      ax[k].ok0 = (flags >> (2 * k)) & 1;
+      ax[k].ok1 = (flags >> (2 * k + 1)) & 1;
+    }
+    mark_tile(ax, dz, D, next_tile_slot, A.next_slot_tile, A.next_nslots, A.slot_count,
+              A.out_src, health);
+    mark_tile(ax, dz + 4, D, next_tile_slot, A.next_slot_tile, A.next_nslots, A.slot_count,
+              A.out_src, health);
   }
 }
 
@@ -992,17 +1024,17 @@ VolumeParams volume_params(const Ctx &c) {
 template <typename real>
 FaceArgs<real> face_args(const Ctx &c, int reset) {
   FaceArgs<real> a;
-  a.fp.a1 = c.iface.alpha[0];
-  a.fp.a2 = c.iface.alpha[1];
-  a.fp.a3 = c.iface.alpha[2];
-  a.fp.eps48 = 48.0 * c.iface.eps;
-  a.fp.xi = c.iface.xi;
+  const double *al = c.iface.alpha;
+  a.fp.a3 = (real)al[2];
+  a.fp.cL0 = (real)(0.5 * (al[0] - al[2]));
+  a.fp.cL1 = (real)(0.25 * (al[0] + al[1]));
+  a.fp.eps48 = (real)(48.0 * c.iface.eps);
+  a.fp.xi = (real)c.iface.xi;
   a.fp.wall_on = c.iface.wall_force_on;
   const int other = c.map ^ 1;
   a.nf = c.nf;
   a.faces = c.faces;
   a.disp = (const Vec4<real> *)c.disp;
-  a.fref = c.fref;
   a.fgeo = (const real *)c.fgeo;
   a.fcontrib = (real *)c.fcontrib;
   a.fnorm = (real *)c.fnorm;
@@ -1041,6 +1073,9 @@ VertexArgs<real> vertex_args(const Ctx &c, int bin) {
   a.nsources = c.counters + 4;
   a.health = c.counters + 3;
   a.zero_counter = bin == 2 ? c.counters + (c.map ^ 1) : nullptr;
+  a.vol_partial = c.vol_partial;
+  a.vp = volume_params(c);
+  a.vcoef = (real *)c.vcoef;
   a.D = dims_of(c);
   return a;
 }
@@ -1060,9 +1095,7 @@ SourceArgs<real> source_args(const Ctx &c) {
   a.stencil = (const StencilRec<real> *)c.stencil;
   a.phi = (const Vec4<real> *)c.phi;
   a.gvol = (const Vec4<real> *)c.gvol;
-  a.vol_partial = c.vol_partial;
-  a.vp = volume_params(c);
-  a.health = c.counters + 3;
+  a.vcoef = (const real *)c.vcoef;
   a.Rslot = (Vec4<real> *)c.Rslot;
   a.out_src = c.out_src[c.map];
   a.D = dims_of(c);

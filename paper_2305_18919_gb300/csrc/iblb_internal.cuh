@@ -149,7 +149,9 @@ struct Ctx {
   double *fref = nullptr;    // [nf][4] reference metric inverse (H11, H12, H22) and A0
   double *xref = nullptr;    // [nv][3] reference vertex positions
   void *disp = nullptr;      // [nv] Vec4: q - xref in the population type (kept by K2)
-  void *fgeo = nullptr;      // [nf][12] reference edges A, B, X0 - c, heights above the walls
+  void *fgeo = nullptr;      // [16][nf] reference edges A, B, X0 - c, heights above the walls,
+                             //   (pad), metric inverse H11 H12 H22 and A0, by component
+  void *vcoef = nullptr;     // kV (V - V0)/V0 of the step, in the population type (K3b writes it)
   int *vf_start = nullptr;   // [nv+1] CSR vertex -> (face*3 + corner)
   int *vf_list = nullptr;    // [3 nf]
   void *fcontrib = nullptr;  // [nf][3 corners][3]: strain + wall force per corner
