@@ -63,8 +63,8 @@ typedef struct {
   int32_t ib_sms;          /* SMs given to the interface chain of iblb_step as a partition of
                               the GPU (green context); the stream-collide passes get the rest.
                               0: when the stream-collide pass moves at least 1 GiB
-                              (2 x 19 x nx ny nz x storage bytes) 24, or 40 with 16-bit
-                              storage; below that 64 (rounded to the device's
+                              (2 x 19 x nx ny nz x storage bytes) 24, 40 with 16-bit
+                              storage and none with FP64; below that 64 (rounded to the device's
                               partition granularity), < 0: no
                               partition (both share all SMs, interface stream at top priority).
                               If the device or driver cannot partition, no partition is used. */

@@ -320,11 +320,15 @@ int iblb_create(const iblb_lattice_desc *d, void *cuda_stream, iblb_ctx **out) {
   // 40 (256^3 FP16: 66.0k against 59.0k on 32). A shorter pass leaves the chain as the
   // critical path, which then takes 64 SMs (128x128x96 FP32 wetting, 1.5 M nodes: 0.090 ms
   // against 0.115 ms on 32 SMs; 32^3 FP64 shear: 0.136 ms against 0.138 ms on 32 and
-  // 0.149 ms unpartitioned).
+  // 0.149 ms unpartitioned). An FP64 pass that long is bound by the FP64 units (1/64 of the
+  // FP32 rate), not by memory, and the interface chain is short beside it: no partition
+  // (256^3 FP64: 7.05 ms per step against 7.30 on 8 interface SMs and 8.20 on 24).
   const size_t pass_bytes = (size_t)2 * iblb::Q * c.ncell * c.pop_size;
   const int want = d->ib_sms != 0 ? d->ib_sms
                    : pass_bytes < ((size_t)1 << 30) ? 64
-                   : (c.pop_size == 2 ? 40 : 24);
+                   : c.pop_size == 2 ? 40
+                   : c.pop_size == 8 ? -1
+                   : 24;
   if (e == cudaSuccess && !(want > 0 && make_partitions(c, want, prio_hi))) {
     e = cudaStreamCreateWithPriority(&c.ib, cudaStreamNonBlocking, prio_hi);
     c.ls = c.stream;
