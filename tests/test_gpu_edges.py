@@ -1,7 +1,8 @@
 """Edge cases of the CUDA path against the FP64 oracle: no steps at all, the smallest lattices
 (a single fluid layer between the walls, the shortest periodic z), the coarsest mesh (the bare
 icosahedron, 12 vertices), and a fluid at rest, which the collision must leave exactly at
-rest (Eq. 10 at u = 0, rho = rho0 is the stored state itself)."""
+rest (Eq. 10 at u = 0, rho = rho0 is the stored state itself). Also the default SM split of
+a context for each lattice size and storage precision."""
 import numpy as np
 import pytest
 
@@ -103,4 +104,25 @@ def test_fields_into_device_buffers():
     assert rho_d.is_cuda and u_d.shape == u.shape
     assert np.array_equal(rho_d.cpu().numpy(), rho)
     assert np.array_equal(u_d.cpu().numpy(), u)
+    lat.close()
+
+
+@pytest.mark.parametrize("shape, precision, expected", [
+    ((256, 256, 256), "fp32", 24),  # 2.5 GB pass: the interface chain fits on 24 SMs
+    ((256, 256, 256), "fp16", 40),  # half the pass: the chain needs more SMs
+    ((256, 256, 256), "fp64", 0),   # FP64-bound pass: no partition
+    ((128, 128, 96), "fp32", 64),   # a short pass leaves the chain as the critical path
+    ((32, 32, 32), "fp64", 64),
+])
+def test_default_interface_partition(shape, precision, expected):
+    """The default SM split of iblb_create follows the size of the stream-collide pass
+    (2 x 19 x nodes x storage bytes, against 1 GiB) and the storage precision; an explicit
+    ib_sms < 0 asks for no partition."""
+    from paper_2305_18919_gb300 import binding
+    nx, ny, nz = shape
+    lat = binding.Lattice(nx, ny, nz, 0.8, precision=precision)
+    assert lat.interface_sms() == expected
+    lat.close()
+    lat = binding.Lattice(nx, ny, nz, 0.8, precision=precision, ib_sms=-1)
+    assert lat.interface_sms() == 0
     lat.close()
