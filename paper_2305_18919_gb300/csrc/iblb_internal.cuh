@@ -64,6 +64,21 @@ struct MultiBlock {
 };
 
 // Instance and local block of this block (every thread of the block must call it).
+// Instance and block of virtual block b, from the block offsets staged in shared memory.
+__device__ __forceinline__ MultiBlock multi_block_of(const int *s_start, int n, int b) {
+  int lo = 0, hi = n;  // the largest lo with start[lo] <= b
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (s_start[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  MultiBlock m;
+  m.inst = lo;
+  m.block = b - s_start[lo];
+  m.nblocks = s_start[lo + 1] - s_start[lo];
+  return m;
+}
+
 __device__ __forceinline__ MultiBlock multi_block(const int *__restrict__ start, int n) {
   __shared__ int s_start[kMultiMax + 1];
   for (int k = threadIdx.x; k <= n; k += blockDim.x) s_start[k] = start[k];
